@@ -1,0 +1,333 @@
+#!/usr/bin/env python
+"""Throughput of the coupled electrohydrodynamic lattice step on GB300.
+
+Workload: the dielectric droplet of the model (arXiv:1712.08494 Sec. III.B
+geometry, 3D): 128^3 periodic box, two Shan-Chen components (G = 4, tau = 1),
+blue drop of radius 24 at the centre, +-1% seeded density noise, two
+monovalent ion species at 1e-3, D = 0.05, Bjerrum length 0.4, permittivity
+ratio 2, applied field 1e-3 along z, Poisson relative residual 1e-6.  A step
+is one full coupled timestep (macro fields, Poisson solve, forces and ion
+fluxes, Nernst-Planck update, collision, streaming).
+
+Prints one JSON line: FP32 MLUPS (value), BF16-storage MLUPS and its speedup
+and deviation from the FP32 run, the roofline of the dominant kernel
+(k_collide) against the measured HBM bandwidth, the end-to-end rate through
+the C-ABI with host buffers, the CPU oracle baseline, clocks and launch count.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "coupled-step MLUPS & % HBM roofline; BF16 vs FP32 speedup at stated error"
+SIZE = 128
+# algorithmic bytes per site of one k_collide launch (two components, two ion
+# species, no colloids): populations read+write, psi_a psi_b, rho_a, eps, phi
+# (FP64), n+ n-, written u and three face fluxes per species
+COLLIDE_BYTES = {"fp32": 2 * 19 * 4 * 2 + 8 + 4 + 4 + 8 + 8 + 12 + 24,
+                 "bf16": 2 * 19 * 2 * 2 + 8 + 4 + 4 + 8 + 8 + 12 + 24}
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
+        int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("step_kernels.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1712_08494_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(prec):
+    """DRAM bytes per k_collide launch from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "k_collide_droplet128.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != kernel_source_hash():
+        return None
+    m = re.search(r"traffic_%s_bytes_per_launch:\s*([0-9.eE+]+)" % prec, txt)
+    return float(m.group(1)) if m else None
+
+
+def cpu_baseline(n, budget_s=30.0):
+    """Time the FP64 CPU oracle, as it stands, on a bounded sample of the same
+    workload: one step of the droplet after one untimed step."""
+    import synth
+    from oracle import OracleSystem
+    w = synth.droplet(n=n, r=24.0 * n / 128.0, prec="fp32")
+    s = OracleSystem(w.params, w.rho, w.n)
+    s.step()
+    t0 = time.perf_counter()
+    s.step()
+    dt = time.perf_counter() - t0
+    return {"value": n ** 3 / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": "1 timed step (after 1 untimed) of the %d^3 droplet, numpy FP64, single thread" % n}
+
+
+def run_reference(args):
+    """CPU oracle timed on the host cores, each step a bounded sample (one
+    oracle step of a reduced droplet box)."""
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return
+    import synth
+    from oracle import OracleSystem
+    n = 32
+    w = synth.droplet(n=n, r=24.0 * n / 128.0, prec="fp32")
+    s = OracleSystem(w.params, w.rho, w.n)
+    t = time.perf_counter()
+    s.step()
+    one = time.perf_counter() - t
+    while n > 8 and one * (args.steps + args.warmup) > 150.0:
+        n //= 2
+        w = synth.droplet(n=n, r=24.0 * n / 128.0, prec="fp32")
+        s = OracleSystem(w.params, w.rho, w.n)
+        t = time.perf_counter()
+        s.step()
+        one = time.perf_counter() - t
+    for _ in range(args.warmup):
+        s.step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        s.step()
+    dt = time.perf_counter() - t0
+    val = n ** 3 * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "dielectric droplet, sampled at %d^3 per step (oracle)" % n},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "each step: one oracle step of the %d^3 droplet" % n},
+            "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import paper_1712_08494_gb300 as pkg
+    import synth
+
+    rank, world, local = env_rank()
+    pkg.build()
+    lbeh = pkg.load()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    stream = torch.cuda.current_stream()
+    n = args.size
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    results = {}
+    fields = {}
+    sampler = None
+    for prec in ("fp32", "bf16"):
+        w = synth.droplet(n=n, r=24.0 * n / 128.0, prec=prec, seed=1 + rank)
+        sysg = lbeh.System(w.params, stream.cuda_stream)
+        sysg.set_fields(rho=list(w.rho), n=list(w.n))
+        sysg.step(args.warmup)
+        torch.cuda.synchronize()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        sysg.profile_enable(True)
+        smp = ClockSampler(local) if prec == "fp32" else None
+        if smp:
+            smp.__enter__()
+        e0.record(stream)
+        rc = sysg.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if smp:
+            smp.__exit__()
+            sampler = smp
+        barrier()
+        torch.cuda.synchronize()
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        prof = sysg.profile_read()
+        obs = sysg.observables()
+        results[prec] = {"ms": ms, "prof": prof, "rc": rc, "obs": obs}
+        fields[prec] = sysg.get(("rho",))["rho"]
+        sysg.close()
+        del sysg
+
+    N = n ** 3
+    ms32 = results["fp32"]["ms"]
+    mlups32 = world * N * args.steps / (ms32 * 1e3)
+    msbf = results["bf16"]["ms"]
+    mlupsbf = world * N * args.steps / (msbf * 1e3)
+    err_bf = max(float(np.abs(fields["bf16"][s] - fields["fp32"][s]).max() / np.abs(fields["fp32"][s]).max())
+                 for s in range(2))
+
+    # end-to-end through the C-ABI with pinned host buffers: every step loads
+    # the state from host memory, advances one step and reads the observables back
+    w = synth.droplet(n=n, r=24.0 * n / 128.0, prec="fp32", seed=1 + rank)
+    host = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
+            for a in (w.rho[0], w.rho[1], w.n[0], w.n[1])]
+    sysg = lbeh.System(w.params, stream.cuda_stream)
+    ke = max(3, min(10, args.steps))
+    for it in range(2 + ke):
+        if it == 2:
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+        sysg.set_fields(rho=host[:2], n=host[2:])
+        sysg.step(1)
+        sysg.observables()
+    torch.cuda.synchronize()
+    te = max_over_ranks(time.perf_counter() - t0)
+    sysg.close()
+    e2e = {"value": world * N * ke / te / 1e6, "unit": "MLUPS",
+           "h2d_bytes_per_step": int(sum(t.numel() * t.element_size() for t in host)),
+           "d2h_bytes_per_step": 16 * 8}
+
+    peak, peak_kind = measured_peaks()
+    prof = results["fp32"]["prof"]
+    calls = max(1, prof["calls"]["collide"])
+    t_coll = prof["ms"]["collide"] / calls * 1e-3
+    achieved = COLLIDE_BYTES["fp32"] * N / t_coll / 1e9
+    profb = results["bf16"]["prof"]
+    t_collb = profb["ms"]["collide"] / max(1, profb["calls"]["collide"]) * 1e-3
+    achievedb = COLLIDE_BYTES["bf16"] * N / t_collb / 1e9
+    tr = ncu_traffic("fp32")
+
+    if rank != 0:
+        return
+    cpu = None if args.no_cpu_baseline else cpu_baseline(n)
+    clocks = sampler.summary() if sampler else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+    total_ms = sum(prof["ms"].values())
+    line = {
+        "metric": METRIC, "value": mlups32, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "dielectric droplet %d^3, 2 components + 2 ion species, E_z=1e-3" % n,
+                   "sites": N, "populations": "fp32", "poisson_tol": 1e-6,
+                   "l2": "inputs larger than L2 (populations %.0f MB)" % (2 * 19 * 4 * N / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "bf16_storage": {"value": mlupsbf, "unit": "MLUPS", "speedup_vs_fp32": mlupsbf / mlups32,
+                         "max_rel_dev_rho_vs_fp32": err_bf, "ms_per_step": msbf / args.steps,
+                         "collide_gbs": achievedb},
+        "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": tr,
+                     "algorithmic_bytes_per_launch": COLLIDE_BYTES["fp32"] * N,
+                     "avg_launch_ms": t_coll * 1e3},
+        "stage_share": {k: (v / total_ms if total_ms else None) for k, v in prof["ms"].items()},
+        "poisson_iters_last": results["fp32"]["obs"].poisson_iters,
+        "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": prof["launches"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=SIZE)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

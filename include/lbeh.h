@@ -1,0 +1,194 @@
+/*
+ * lbeh -- coupled electrohydrodynamic lattice step on one NVIDIA GB300 (sm_103a).
+ *
+ * The library advances the model of Rivas, Frijters, Pagonabarraga and
+ * Harting, "Mesoscopic electrohydrodynamic simulations of binary colloidal
+ * suspensions" (arXiv:1712.08494), Sec. II, one lattice timestep at a time:
+ *   - two-component D3Q19 BGK stream-collide with Shan-Chen pseudopotential
+ *     forcing (Sec. II.A, II.C eq. shanChenForce),
+ *   - electric body forces: ion friction and Kelvin force (Sec. II.C),
+ *   - link-flux Nernst-Planck update of two monovalent ion species on the
+ *     D3Q7 faces with solid-fraction weighting (Sec. II.B, II.E),
+ *   - variable-permittivity Poisson solve for the potential (Sec. II.B, II.D),
+ *   - halfway bounce-back on colloid boundary links with the moving-wall term
+ *     and momentum exchange, colloid projection and motion (Sec. II.E).
+ *
+ * Conventions for every entry point:
+ *   - lattice units: dx = dt = e = beta = rho0 = 1;
+ *   - scalar fields are nz*ny*nx arrays indexed (z*ny + y)*nx + x (x fastest);
+ *     multi-component fields are stacked along a leading index;
+ *   - component 0 is "a" (red, water), component 1 is "b" (blue, oil);
+ *     ion species 0 is the cation (z=+1), species 1 the anion (z=-1);
+ *   - D3Q19 velocity order: 0 rest; 1..6 = +x -x +y -y +z -z; then
+ *     (1,1,0) (-1,-1,0) (1,-1,0) (-1,1,0) (1,0,1) (-1,0,-1) (1,0,-1) (-1,0,1)
+ *     (0,1,1) (0,-1,-1) (0,1,-1) (0,-1,1);
+ *   - every function returns LBEH_OK (0) or a negative LBEH_ERR_* code and
+ *     never aborts; the caller owns every buffer it passes, the handle owns
+ *     all device state it allocates; a handle is bound to one CUDA stream and
+ *     must not be used from two host threads at once.
+ */
+#ifndef LBEH_H
+#define LBEH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LBEH_OK 0
+#define LBEH_ERR_INVALID_ARG (-1)
+#define LBEH_ERR_OOM (-2)
+#define LBEH_ERR_CUDA (-3)
+#define LBEH_ERR_POISSON_NOT_CONVERGED (-4)
+#define LBEH_ERR_NONFINITE (-5)
+#define LBEH_ERR_BARRIER_TIMEOUT (-6)
+#define LBEH_ERR_UNSUPPORTED (-7)
+
+/* Arithmetic and storage of the populations.  FP64: all FP64.  FP32: FP32
+ * compute and storage.  *_BF16STORE / *_FP16STORE: FP32 compute, populations
+ * stored as f - w_q rho0_shift[sigma] in bf16 / fp16.  The potential is held
+ * in FP64 in every mode (FP32 multigrid corrections with FP64 residuals). */
+typedef enum {
+  LBEH_FP64 = 0,
+  LBEH_FP32 = 1,
+  LBEH_FP32_BF16STORE = 2,
+  LBEH_FP32_FP16STORE = 3
+} lbeh_precision;
+
+/* Model parameters (Sec. II).  Unused members may be zero. */
+typedef struct lbeh_params {
+  int nx, ny, nz;       /* periodic box, each >= 2 */
+  int ncomp;            /* fluid components: 1 or 2 */
+  int nions;            /* ion species: 0 or 2 */
+  int prec;             /* lbeh_precision */
+  double tau;           /* BGK relaxation time, equal for both components (Sec. II.A) */
+  double G;             /* fluid-fluid Shan-Chen coupling G_ab, D3Q19-weighted (Sec. II.C) */
+  double rho0_shift[2]; /* reduced-precision storage offset per component */
+  double D;             /* ion diffusivity (Sec. II.B eq. ionicflux) */
+  double bjerrum;       /* Bjerrum length l_B; eps_ref = 1/(4 pi l_B) (Sec. III.E) */
+  double eps_r[2];      /* relative permittivity of components a, b (eq. dielectric_constant) */
+  double eps_r_colloid; /* relative permittivity of the colloids (Sec. II.E) */
+  double dmu[2];        /* Gibbs transfer energies of cation, anion (eq. solvation_potential) */
+  double drho_a;        /* Delta rho^a of eq. solvation_potential */
+  double E_ext[3];      /* applied uniform field (Sec. II.B potential split) */
+  double poisson_tol;   /* stop when ||b - A phi||_2 / ||b||_2 < tol */
+  int poisson_max_iter; /* multigrid cycles per step before LBEH_ERR_POISSON_NOT_CONVERGED */
+  int ncolloid_max;     /* capacity of the colloid table (0: no colloids) */
+  double rho_p;         /* colloid mass density, m = rho_p (4/3) pi r^3 (Sec. II.E) */
+  double k_hertz;       /* Hertz stiffness (eq. colloid_interaction) */
+  int psi_subdiv;       /* h: solid fraction from (h+1)^3 sub-cube centres (Sec. II.E) */
+  int colloids_move;    /* 0: fixed colloids; 1: velocity-Verlet motion and remap */
+  void *stream;         /* cudaStream_t all work is issued on (NULL: legacy default stream) */
+} lbeh_params;
+
+#define LBEH_F64 0
+#define LBEH_F32 1
+
+/* Field buffers for lbeh_set_fields / lbeh_get_fields.  `dtype` (LBEH_F64 or
+ * LBEH_F32) is the element type of rho, u, f, n and phi; `on_device` says
+ * whether those pointers are device (1) or host (0) memory.  Colloid arrays
+ * are always host FP64.  NULL members are skipped. */
+typedef struct lbeh_fields {
+  int dtype;
+  int on_device;
+  void *rho[2];  /* component densities; set: equilibrium initialisation */
+  void *u;       /* [3][N] velocity for the equilibrium initialisation; get: physical velocity */
+  void *f;       /* [ncomp][19][N] populations (set: overrides rho/u) */
+  void *n[2];    /* cation, anion concentrations */
+  void *phi;     /* internal potential (set: warm start) */
+  int ncolloid;  /* number of colloids (<= ncolloid_max) */
+  double *cx;    /* [ncolloid][3] centres (x, y, z) */
+  double *cv;    /* [ncolloid][3] velocities */
+  double *cq;    /* [ncolloid] total charges */
+  double *cr;    /* [ncolloid] radii */
+  double *cf;    /* get only: [ncolloid][3] total force of the last step */
+} lbeh_fields;
+
+/* Observables, all FP64. */
+typedef struct lbeh_obs {
+  double mass[2];        /* sum of rho^sigma over fluid nodes */
+  double ions[2];        /* sum of n^+, n^- */
+  double charge;         /* sum of n^+ - n^- plus the colloid charge */
+  double momentum[3];    /* fluid momentum sum_x sum_sigma sum_q f c_q */
+  double deformation;    /* (sqrt(Mzz)-sqrt(Mxx))/(sqrt(Mzz)+sqrt(Mxx)), weight max(0,c) */
+  double centroid[3];    /* weighted centre of the drop */
+  double colloid_v[3];   /* mean colloid velocity */
+  double poisson_relres; /* relative residual of the last solve */
+  int poisson_iters;     /* multigrid cycles of the last solve */
+  int status;            /* sticky device status (LBEH_OK or an error code) */
+  long long steps;       /* steps taken since the last lbeh_set_fields */
+} lbeh_obs;
+
+typedef struct lbeh_handle lbeh_handle;
+
+/* Allocate the device state of one lattice system (model of Sec. II).
+ * Copies *p.  Errors: INVALID_ARG (bad sizes or flags), OOM, CUDA. */
+int lbeh_create(const lbeh_params *p, lbeh_handle **out);
+
+/* Load the state: colloids first (projection of Sec. II.E: solid nodes,
+ * solid fraction, surface charge), then populations as the second-order
+ * equilibrium of Sec. II.A at rho (and u, zero if NULL) on fluid nodes, or
+ * the populations themselves; ions are zeroed on solid nodes.  Synchronous
+ * with respect to the host buffers.  Errors: INVALID_ARG, CUDA. */
+int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in);
+
+/* Copy the state out (densities and physical velocity of the last step,
+ * populations with the storage offset added back, ions, potential, colloid
+ * table and forces).  Synchronises the handle's stream. */
+int lbeh_get_fields(lbeh_handle *h, lbeh_fields *out);
+
+/* Advance nsteps coupled timesteps (Sec. II: macro fields, Poisson solve,
+ * ion fluxes, forces, Nernst-Planck update, forced BGK collision, streaming
+ * with halfway bounce-back, colloid motion).  Work is issued on the handle's
+ * stream; a Poisson solve that reaches poisson_max_iter cycles returns
+ * LBEH_ERR_POISSON_NOT_CONVERGED and leaves the sticky status set. */
+int lbeh_step(lbeh_handle *h, int nsteps);
+
+/* Conserved sums, drop deformation and colloid drift, reduced on the device
+ * in FP64 in a fixed order (bitwise reproducible).  Synchronises. */
+int lbeh_observables(lbeh_handle *h, lbeh_obs *out);
+
+/* Auxiliary read-outs for validation (host destination, FP64 unless noted):
+ * fields of the last step or of the current geometry. */
+#define LBEH_AUX_SOLID 0   /* uint8 [N] solid mask */
+#define LBEH_AUX_OWNER 1   /* int32 [N] colloid id or -1 */
+#define LBEH_AUX_PSI_S 2   /* [N] solid fraction */
+#define LBEH_AUX_SURFACE 3 /* uint8 [N] surface (interface solid) nodes */
+#define LBEH_AUX_QC 4      /* [N] colloid charge */
+#define LBEH_AUX_EPS 5     /* [N] permittivity of the last step */
+#define LBEH_AUX_Q 6       /* [N] charge density of the last step */
+#define LBEH_AUX_RHO_V 7   /* [ncomp][N] densities incl. virtual densities */
+#define LBEH_AUX_U 8       /* [3][N] physical velocity of the last step */
+int lbeh_get_aux(lbeh_handle *h, int which, void *out_host);
+
+/* Per-stage device time of lbeh_step, measured with CUDA events recorded on
+ * the handle's stream around each stage, and the number of kernels the
+ * library launched.  lbeh_profile_enable(h, 1) resets and starts the
+ * accumulation (0 stops it); lbeh_profile_read synchronises the stream and
+ * returns the totals since the last enable.  Stages: */
+#define LBEH_STAGE_MACRO 0   /* macro fields + virtual densities */
+#define LBEH_STAGE_POISSON 1 /* Poisson solve (includes its host convergence checks) */
+#define LBEH_STAGE_COLLIDE 2 /* fused forces / fluxes / collision / streaming / bounce-back */
+#define LBEH_STAGE_NP 3      /* Nernst-Planck update */
+#define LBEH_STAGE_COLLOID 4 /* colloid momentum exchange, forces, motion */
+#define LBEH_NSTAGES 5
+typedef struct lbeh_profile {
+  double ms[LBEH_NSTAGES];       /* summed device time per stage */
+  long long calls[LBEH_NSTAGES]; /* stage executions */
+  long long launches;            /* kernels launched by the library */
+} lbeh_profile;
+int lbeh_profile_enable(lbeh_handle *h, int on);
+int lbeh_profile_read(lbeh_handle *h, lbeh_profile *out);
+
+/* Release all device state. */
+void lbeh_destroy(lbeh_handle *h);
+
+/* Static description of a status code. */
+const char *lbeh_status_string(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBEH_H */

@@ -1,0 +1,101 @@
+// Host-side interfaces between the translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <atomic>
+
+#include "common.cuh"
+
+namespace lbeh {
+
+// Kernel launches made by the library (process-wide, read as differences).
+extern std::atomic<long long> g_launches;
+inline void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// Everything a launch needs: sizes, model constants and device pointers.
+// Field pointers are of the compute type T (double for FP64, float otherwise)
+// unless noted; populations are of the storage type of the precision mode.
+struct Ctx {
+  Dims d;
+  int ncomp = 1, nions = 0, prec = LBEH_FP32;
+  bool solids = false;      // colloids present
+  bool has_field = false;   // potential or applied field present
+  bool solvation = false;   // dmu != 0
+  double tau = 1, G = 0, D = 0;
+  double gas[2] = {0, 0};   // G_{a+-} = dmu / (drho_a c_s^2)
+  double dmd[2] = {0, 0};   // dmu / drho_a
+  double eps_a = 0, eps_b = 0, eps_p = 0, eps_bar = 0;
+  double Eext[3] = {0, 0, 0};
+  double shift[2] = {0, 0};
+  int h = 3;                // solid-fraction subdivision
+
+  void *f[2] = {nullptr, nullptr};  // populations ping-pong [ncomp][19][N]
+  int cur = 0;
+  void *rho = nullptr;     // [ncomp][N] incl. virtual densities
+  void *psi = nullptr;     // [ncomp][N]
+  void *eps = nullptr;     // [N]
+  void *q = nullptr;       // [N]
+  void *n[2] = {nullptr, nullptr};  // ions ping-pong [2][N]
+  int ncur = 0;
+  void *u = nullptr;       // [3][N]
+  void *flux = nullptr;    // [2][3][N]
+  void *psi_s = nullptr;   // [N]
+  void *psi_f = nullptr;   // [N]
+  void *qc = nullptr;      // [N]
+  double *phi = nullptr;   // [N]
+  uint8_t *solid = nullptr, *surface = nullptr;
+  int *owner = nullptr;
+
+  int ncoll = 0, ncoll_max = 0;
+  double *cx = nullptr, *cv = nullptr, *cq = nullptr, *cr = nullptr;  // device colloid table
+  double *cforce = nullptr;  // [ncoll][3]
+  int *ccount = nullptr;     // [ncoll] surface node counts
+  int *status = nullptr;     // device status word
+
+  long long launches = 0;    // kernels launched (all launch sites count here)
+  double *red = nullptr;     // reduction scratch (FP64)
+  size_t red_len = 0;
+  cudaStream_t s = nullptr;
+};
+
+// Per-storage-type kernels (defined in step_<prec>.cu).
+struct PrecOps {
+  void (*init_eq)(Ctx &, const double *rho, const double *u);  // rho [ncomp][N], u [3][N] or null (FP64 device)
+  void (*init_f)(Ctx &, const double *f);                      // [ncomp][19][N] FP64 device
+  void (*get_f)(Ctx &, double *f);                             // [ncomp][19][N] FP64 device
+  void (*get_rho)(Ctx &, double *rho);                         // [ncomp][N] FP64 device
+  void (*macro)(Ctx &);
+  void (*virt)(Ctx &);
+  void (*collide)(Ctx &);
+  void (*np)(Ctx &);
+  void (*obs_partials)(Ctx &, double *partials, int nblocks);  // kObsLen doubles per block
+  void (*colloid_bb)(Ctx &);                                    // momentum exchange into cforce
+};
+PrecOps ops_f64();
+PrecOps ops_f32();
+PrecOps ops_bf16();
+PrecOps ops_f16();
+
+constexpr int kObsLen = 16;  // see step_kernels.cuh obs layout
+constexpr int kRedBlocks = 512;
+
+// Geometry (geometry.cu).
+void geometry_build(Ctx &c);  // solid, owner, psi_s, psi_f, surface, ccount, qc
+
+// Poisson (poisson.cu).
+struct Poisson;
+Poisson *poisson_create(const Ctx &c, int fp64);
+void poisson_destroy(Poisson *p);
+// Solves for c.phi from c.eps, c.q; returns iterations (negative on CUDA error).
+int poisson_solve(Poisson *p, Ctx &c, double tol, int max_iter, double *relres);
+
+// Deterministic FP64 reductions (reduce.cu).
+void reduce_partials_final(const double *partials, int nblocks, int len, double *out, cudaStream_t s);
+double dot_f64(const double *a, const double *b, long long n, double *scratch, cudaStream_t s);
+double sum_f64(const double *a, long long n, double *scratch, cudaStream_t s);
+
+inline int grid_for(long long n, int block) { return int((n + block - 1) / block); }
+
+}  // namespace lbeh

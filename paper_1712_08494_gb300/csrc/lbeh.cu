@@ -1,0 +1,606 @@
+// C-ABI of the coupled electrohydrodynamic lattice step (include/lbeh.h).
+//
+// The handle owns the device state of one periodic lattice system and issues
+// all work on the caller's stream.  One step (Sec. II): macro fields and
+// virtual densities, Poisson solve, fused forces/fluxes/collision/streaming
+// with bounce-back, Nernst-Planck update, colloid momentum exchange.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+using namespace lbeh;
+
+struct lbeh_handle {
+  lbeh_params p;
+  Ctx c;
+  PrecOps ops;
+  Poisson *pois = nullptr;
+  std::vector<void *> allocs;
+  int status = LBEH_OK;
+  long long steps = 0;
+  int last_iters = 0;
+  double last_relres = 0.0;
+  bool loaded = false;
+  std::vector<double> hx, hv, hq, hr, hf;  // host copy of the colloid table
+  // profiling: event pairs per executed stage, accumulated on read
+  struct Mark {
+    int stage;
+    cudaEvent_t a, b;
+  };
+  bool prof = false;
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[LBEH_NSTAGES] = {0};
+  long long prof_calls[LBEH_NSTAGES] = {0};
+  long long launches0 = 0;
+};
+
+std::atomic<long long> lbeh::g_launches{0};
+
+namespace {
+
+template <typename A, typename B> __global__ void k_cvt(const A *__restrict__ a, B *__restrict__ b, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = B(a[i]);
+}
+
+template <typename T>
+__global__ void k_mask_fluid(T *__restrict__ a, const uint8_t *__restrict__ solid, long long N, int ncomp) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N || !solid[i]) return;
+  for (int s = 0; s < ncomp; ++s) a[s * N + i] = T(0);
+}
+
+inline bool cuda_ok(cudaError_t e) { return e == cudaSuccess; }
+
+cudaEvent_t take_event(lbeh_handle *h) {
+  if (!h->pool.empty()) {
+    cudaEvent_t e = h->pool.back();
+    h->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void flush_marks(lbeh_handle *h) {
+  if (h->marks.empty()) return;
+  cudaStreamSynchronize(h->c.s);
+  for (auto &m : h->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+      h->prof_ms[m.stage] += ms;
+      h->prof_calls[m.stage] += 1;
+    }
+    h->pool.push_back(m.a);
+    h->pool.push_back(m.b);
+  }
+  h->marks.clear();
+}
+
+struct StageTimer {
+  lbeh_handle *h;
+  lbeh_handle::Mark m;
+  StageTimer(lbeh_handle *hh, int stage) : h(hh) {
+    if (!h->prof) return;
+    m.stage = stage;
+    m.a = take_event(h);
+    m.b = take_event(h);
+    cudaEventRecord(m.a, h->c.s);
+  }
+  ~StageTimer() {
+    if (!h->prof) return;
+    cudaEventRecord(m.b, h->c.s);
+    h->marks.push_back(m);
+    if (h->marks.size() > 8192) flush_marks(h);
+  }
+};
+
+void *dalloc(lbeh_handle *h, size_t bytes) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  h->allocs.push_back(p);
+  return p;
+}
+
+size_t pop_bytes(int prec) { return prec == LBEH_FP64 ? 8 : (prec == LBEH_FP32 ? 4 : 2); }
+
+// Stage `count` elements of the caller's buffer as FP64 on the device.
+// Returns a device pointer (the caller's own if it already is FP64 device
+// memory) and records temporaries in `tmp`.
+const double *stage_in(lbeh_handle *h, const void *src, int dtype, int on_device, long long count,
+                       std::vector<void *> &tmp) {
+  cudaStream_t s = h->c.s;
+  if (on_device && dtype == LBEH_F64) return (const double *)src;
+  double *out = nullptr;
+  if (cudaMalloc(&out, count * 8) != cudaSuccess) return nullptr;
+  tmp.push_back(out);
+  if (dtype == LBEH_F64) {
+    cudaMemcpyAsync(out, src, count * 8, cudaMemcpyHostToDevice, s);
+    return out;
+  }
+  const float *fsrc = (const float *)src;
+  if (!on_device) {
+    float *fd = nullptr;
+    if (cudaMalloc(&fd, count * 4) != cudaSuccess) return nullptr;
+    tmp.push_back(fd);
+    cudaMemcpyAsync(fd, src, count * 4, cudaMemcpyHostToDevice, s);
+    fsrc = fd;
+  }
+  count_launch(), k_cvt<float, double><<<grid_for(count, 256), 256, 0, s>>>(fsrc, out, count);
+  return out;
+}
+
+// Copy `count` FP64 device values to the caller's buffer in its dtype.
+bool stage_out(lbeh_handle *h, const double *dsrc, void *dst, int dtype, int on_device, long long count,
+               std::vector<void *> &tmp) {
+  cudaStream_t s = h->c.s;
+  if (dtype == LBEH_F64) {
+    return cuda_ok(cudaMemcpyAsync(dst, dsrc, count * 8,
+                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  }
+  float *fd = (float *)dst;
+  if (!on_device) {
+    if (cudaMalloc(&fd, count * 4) != cudaSuccess) return false;
+    tmp.push_back(fd);
+  }
+  count_launch(), k_cvt<double, float><<<grid_for(count, 256), 256, 0, s>>>(dsrc, fd, count);
+  if (!on_device) return cuda_ok(cudaMemcpyAsync(dst, fd, count * 4, cudaMemcpyDeviceToHost, s));
+  return true;
+}
+
+// FP64 device copy of a compute-type field.
+const double *as_f64(lbeh_handle *h, const void *src, long long count, std::vector<void *> &tmp) {
+  if (h->c.prec == LBEH_FP64) return (const double *)src;
+  double *out = nullptr;
+  if (cudaMalloc(&out, count * 8) != cudaSuccess) return nullptr;
+  tmp.push_back(out);
+  count_launch(), k_cvt<float, double><<<grid_for(count, 256), 256, 0, h->c.s>>>((const float *)src, out, count);
+  return out;
+}
+
+void to_compute(lbeh_handle *h, const double *src, void *dst, long long count) {
+  if (h->c.prec == LBEH_FP64)
+    cudaMemcpyAsync(dst, src, count * 8, cudaMemcpyDeviceToDevice, h->c.s);
+  else
+    count_launch(), k_cvt<double, float><<<grid_for(count, 256), 256, 0, h->c.s>>>(src, (float *)dst, count);
+}
+
+void free_tmp(lbeh_handle *h, std::vector<void *> &tmp) {
+  cudaStreamSynchronize(h->c.s);
+  for (void *t : tmp) cudaFree(t);
+  tmp.clear();
+}
+
+int check_params(const lbeh_params *p) {
+  if (!p) return LBEH_ERR_INVALID_ARG;
+  if (p->nx < 2 || p->ny < 2 || p->nz < 2) return LBEH_ERR_INVALID_ARG;
+  if (p->ncomp != 1 && p->ncomp != 2) return LBEH_ERR_INVALID_ARG;
+  if (p->nions != 0 && p->nions != 2) return LBEH_ERR_INVALID_ARG;
+  if (p->prec < LBEH_FP64 || p->prec > LBEH_FP32_FP16STORE) return LBEH_ERR_INVALID_ARG;
+  if (!(p->tau > 0.5)) return LBEH_ERR_INVALID_ARG;
+  if (p->nions && !(p->D > 0.0)) return LBEH_ERR_INVALID_ARG;
+  if ((p->nions || p->ncolloid_max > 0) && !(p->bjerrum > 0.0)) return LBEH_ERR_INVALID_ARG;
+  if (p->nions && (p->dmu[0] != 0.0 || p->dmu[1] != 0.0) && p->drho_a == 0.0) return LBEH_ERR_INVALID_ARG;
+  if (p->ncolloid_max < 0 || p->psi_subdiv < 0 || p->psi_subdiv > 15) return LBEH_ERR_INVALID_ARG;
+  if (p->poisson_max_iter < 0) return LBEH_ERR_INVALID_ARG;
+  return LBEH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *lbeh_status_string(int code) {
+  switch (code) {
+    case LBEH_OK: return "ok";
+    case LBEH_ERR_INVALID_ARG: return "invalid argument";
+    case LBEH_ERR_OOM: return "out of device memory";
+    case LBEH_ERR_CUDA: return "CUDA error";
+    case LBEH_ERR_POISSON_NOT_CONVERGED: return "Poisson solve did not reach its tolerance";
+    case LBEH_ERR_NONFINITE: return "non-finite value in the state";
+    case LBEH_ERR_BARRIER_TIMEOUT: return "device wait timed out";
+    case LBEH_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown status";
+  }
+}
+
+int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
+  if (!out) return LBEH_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = check_params(p);
+  if (rc) return rc;
+  lbeh_handle *h = new (std::nothrow) lbeh_handle;
+  if (!h) return LBEH_ERR_OOM;
+  h->p = *p;
+  Ctx &c = h->c;
+  c.d = Dims{p->nx, p->ny, p->nz, (long long)p->nx * p->ny * p->nz};
+  c.ncomp = p->ncomp;
+  c.nions = p->nions;
+  c.prec = p->prec;
+  c.s = (cudaStream_t)p->stream;
+  c.tau = p->tau;
+  c.G = p->ncomp == 2 ? p->G : 0.0;
+  c.D = p->D;
+  const double eps_ref = p->bjerrum > 0 ? 1.0 / (4.0 * M_PI * p->bjerrum) : 0.0;
+  c.eps_a = p->eps_r[0] * eps_ref;
+  c.eps_b = p->eps_r[1] * eps_ref;
+  c.eps_p = p->eps_r_colloid * eps_ref;
+  c.eps_bar = 0.5 * (c.eps_a + c.eps_b);
+  for (int s = 0; s < 2; ++s) {
+    c.dmd[s] = p->nions && p->drho_a != 0.0 ? p->dmu[s] / p->drho_a : 0.0;
+    c.gas[s] = c.dmd[s] * 3.0;  // G_{a+-} = dmu / (drho_a c_s^2)
+    c.shift[s] = (p->prec == LBEH_FP32_BF16STORE || p->prec == LBEH_FP32_FP16STORE) ? p->rho0_shift[s] : 0.0;
+  }
+  c.solvation = p->nions && (p->dmu[0] != 0.0 || p->dmu[1] != 0.0);
+  for (int a = 0; a < 3; ++a) c.Eext[a] = p->E_ext[a];
+  const bool eext = p->E_ext[0] != 0.0 || p->E_ext[1] != 0.0 || p->E_ext[2] != 0.0;
+  c.has_field = p->nions > 0 || p->ncolloid_max > 0 || eext;
+  c.h = p->psi_subdiv;
+  c.ncoll_max = p->ncolloid_max;
+  switch (p->prec) {
+    case LBEH_FP64: h->ops = ops_f64(); break;
+    case LBEH_FP32: h->ops = ops_f32(); break;
+    case LBEH_FP32_BF16STORE: h->ops = ops_bf16(); break;
+    default: h->ops = ops_f16(); break;
+  }
+  const long long N = c.d.N;
+  const size_t T = p->prec == LBEH_FP64 ? 8 : 4;
+  const size_t pb = pop_bytes(p->prec) * 19 * p->ncomp * N;
+  bool ok = true;
+  ok &= (c.f[0] = dalloc(h, pb)) != nullptr;
+  ok &= (c.f[1] = dalloc(h, pb)) != nullptr;
+  ok &= (c.rho = dalloc(h, T * p->ncomp * N)) != nullptr;
+  ok &= (c.psi = dalloc(h, T * p->ncomp * N)) != nullptr;
+  ok &= (c.eps = dalloc(h, T * N)) != nullptr;
+  ok &= (c.q = dalloc(h, T * N)) != nullptr;
+  ok &= (c.u = dalloc(h, T * 3 * N)) != nullptr;
+  ok &= (c.phi = (double *)dalloc(h, 8 * N)) != nullptr;
+  ok &= (c.psi_s = dalloc(h, T * N)) != nullptr;
+  ok &= (c.psi_f = dalloc(h, T * N)) != nullptr;
+  ok &= (c.qc = dalloc(h, T * N)) != nullptr;
+  ok &= (c.solid = (uint8_t *)dalloc(h, N)) != nullptr;
+  ok &= (c.surface = (uint8_t *)dalloc(h, N)) != nullptr;
+  ok &= (c.owner = (int *)dalloc(h, 4 * N)) != nullptr;
+  if (p->nions) {
+    ok &= (c.n[0] = dalloc(h, T * 2 * N)) != nullptr;
+    ok &= (c.n[1] = dalloc(h, T * 2 * N)) != nullptr;
+    ok &= (c.flux = dalloc(h, T * 6 * N)) != nullptr;
+  }
+  const int nc = p->ncolloid_max > 0 ? p->ncolloid_max : 1;
+  ok &= (c.cx = (double *)dalloc(h, 8 * 3 * nc)) != nullptr;
+  ok &= (c.cv = (double *)dalloc(h, 8 * 3 * nc)) != nullptr;
+  ok &= (c.cq = (double *)dalloc(h, 8 * nc)) != nullptr;
+  ok &= (c.cr = (double *)dalloc(h, 8 * nc)) != nullptr;
+  ok &= (c.cforce = (double *)dalloc(h, 8 * 3 * nc)) != nullptr;
+  ok &= (c.ccount = (int *)dalloc(h, 4 * nc)) != nullptr;
+  ok &= (c.status = (int *)dalloc(h, sizeof(int))) != nullptr;
+  c.red_len = (size_t)kRedBlocks * kObsLen + 64;
+  ok &= (c.red = (double *)dalloc(h, 8 * c.red_len)) != nullptr;
+  if (ok && c.has_field) {
+    h->pois = poisson_create(c, p->prec == LBEH_FP64);
+    ok &= h->pois != nullptr;
+  }
+  if (!ok) {
+    lbeh_destroy(h);
+    return LBEH_ERR_OOM;
+  }
+  cudaMemsetAsync(c.u, 0, T * 3 * N, c.s);
+  cudaMemsetAsync(c.phi, 0, 8 * N, c.s);
+  cudaMemsetAsync(c.status, 0, sizeof(int), c.s);
+  cudaMemsetAsync(c.cv, 0, 8 * 3 * nc, c.s);
+  cudaMemsetAsync(c.cforce, 0, 8 * 3 * nc, c.s);
+  if (p->nions) {
+    cudaMemsetAsync(c.flux, 0, T * 6 * N, c.s);
+    cudaMemsetAsync(c.n[0], 0, T * 2 * N, c.s);
+  }
+  geometry_build(c);  // empty geometry: all fluid, psi_f = 1
+  if (cudaStreamSynchronize(c.s) != cudaSuccess) {
+    lbeh_destroy(h);
+    return LBEH_ERR_CUDA;
+  }
+  *out = h;
+  return LBEH_OK;
+}
+
+int lbeh_profile_enable(lbeh_handle *h, int on) {
+  if (!h) return LBEH_ERR_INVALID_ARG;
+  flush_marks(h);
+  for (int k = 0; k < LBEH_NSTAGES; ++k) {
+    h->prof_ms[k] = 0.0;
+    h->prof_calls[k] = 0;
+  }
+  h->prof = on != 0;
+  h->launches0 = g_launches.load();
+  return LBEH_OK;
+}
+
+int lbeh_profile_read(lbeh_handle *h, lbeh_profile *out) {
+  if (!h || !out) return LBEH_ERR_INVALID_ARG;
+  flush_marks(h);
+  for (int k = 0; k < LBEH_NSTAGES; ++k) {
+    out->ms[k] = h->prof_ms[k];
+    out->calls[k] = h->prof_calls[k];
+  }
+  out->launches = g_launches.load() - h->launches0;
+  return cudaGetLastError() == cudaSuccess ? LBEH_OK : LBEH_ERR_CUDA;
+}
+
+void lbeh_destroy(lbeh_handle *h) {
+  if (!h) return;
+  if (h->c.s) cudaStreamSynchronize(h->c.s);
+  flush_marks(h);
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  poisson_destroy(h->pois);
+  for (void *a : h->allocs) cudaFree(a);
+  delete h;
+}
+
+int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
+  if (!h || !in) return LBEH_ERR_INVALID_ARG;
+  if (in->dtype != LBEH_F64 && in->dtype != LBEH_F32) return LBEH_ERR_INVALID_ARG;
+  Ctx &c = h->c;
+  const long long N = c.d.N;
+  if (in->ncolloid < 0 || in->ncolloid > c.ncoll_max) return LBEH_ERR_INVALID_ARG;
+  if (in->ncolloid > 0 && (!in->cx || !in->cr)) return LBEH_ERR_INVALID_ARG;
+  if (!in->f && !in->rho[0]) return LBEH_ERR_INVALID_ARG;
+  if (!in->f && c.ncomp == 2 && !in->rho[1]) return LBEH_ERR_INVALID_ARG;
+  if (c.nions && (!in->n[0] || !in->n[1])) return LBEH_ERR_INVALID_ARG;
+  std::vector<void *> tmp;
+
+  // colloids and geometry
+  const int nc = in->ncolloid;
+  h->hx.assign(3 * nc, 0.0);
+  h->hv.assign(3 * nc, 0.0);
+  h->hq.assign(nc, 0.0);
+  h->hr.assign(nc, 0.0);
+  h->hf.assign(3 * nc, 0.0);
+  for (int j = 0; j < nc; ++j) {
+    for (int a = 0; a < 3; ++a) {
+      h->hx[3 * j + a] = in->cx[3 * j + a];
+      h->hv[3 * j + a] = in->cv ? in->cv[3 * j + a] : 0.0;
+    }
+    h->hq[j] = in->cq ? in->cq[j] : 0.0;
+    h->hr[j] = in->cr[j];
+    if (!(h->hr[j] > 0.0)) return LBEH_ERR_INVALID_ARG;
+  }
+  c.ncoll = nc;
+  c.solids = nc > 0;
+  if (nc) {
+    cudaMemcpyAsync(c.cx, h->hx.data(), 8 * 3 * nc, cudaMemcpyHostToDevice, c.s);
+    cudaMemcpyAsync(c.cv, h->hv.data(), 8 * 3 * nc, cudaMemcpyHostToDevice, c.s);
+    cudaMemcpyAsync(c.cq, h->hq.data(), 8 * nc, cudaMemcpyHostToDevice, c.s);
+    cudaMemcpyAsync(c.cr, h->hr.data(), 8 * nc, cudaMemcpyHostToDevice, c.s);
+    cudaMemsetAsync(c.cforce, 0, 8 * 3 * nc, c.s);
+  }
+  geometry_build(c);
+
+  // populations
+  c.cur = 0;
+  c.ncur = 0;
+  if (in->f) {
+    const double *fd = stage_in(h, in->f, in->dtype, in->on_device, (long long)c.ncomp * 19 * N, tmp);
+    if (!fd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
+    h->ops.init_f(c, fd);
+  } else {
+    std::vector<void *> t2;
+    double *rd = nullptr;
+    if (cudaMalloc(&rd, 8 * c.ncomp * N) != cudaSuccess) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
+    tmp.push_back(rd);
+    for (int s = 0; s < c.ncomp; ++s) {
+      const double *r = stage_in(h, in->rho[s], in->dtype, in->on_device, N, tmp);
+      if (!r) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
+      cudaMemcpyAsync(rd + s * N, r, 8 * N, cudaMemcpyDeviceToDevice, c.s);
+    }
+    const double *ud = nullptr;
+    if (in->u) {
+      ud = stage_in(h, in->u, in->dtype, in->on_device, 3 * N, tmp);
+      if (!ud) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
+    }
+    h->ops.init_eq(c, rd, ud);
+  }
+  // ions, zero on solid nodes
+  if (c.nions) {
+    for (int s = 0; s < 2; ++s) {
+      const double *nd = stage_in(h, in->n[s], in->dtype, in->on_device, N, tmp);
+      if (!nd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
+      to_compute(h, nd, (char *)c.n[0] + (size_t)s * N * (c.prec == LBEH_FP64 ? 8 : 4), N);
+    }
+    if (c.solids) {
+      if (c.prec == LBEH_FP64)
+        count_launch(), k_mask_fluid<double><<<grid_for(N, 256), 256, 0, c.s>>>((double *)c.n[0], c.solid, N, 2);
+      else
+        count_launch(), k_mask_fluid<float><<<grid_for(N, 256), 256, 0, c.s>>>((float *)c.n[0], c.solid, N, 2);
+    }
+  }
+  // potential (warm start)
+  if (in->phi) {
+    const double *pd = stage_in(h, in->phi, in->dtype, in->on_device, N, tmp);
+    if (!pd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
+    cudaMemcpyAsync(c.phi, pd, 8 * N, cudaMemcpyDeviceToDevice, c.s);
+  } else {
+    cudaMemsetAsync(c.phi, 0, 8 * N, c.s);
+  }
+  cudaMemsetAsync(c.u, 0, (c.prec == LBEH_FP64 ? 8 : 4) * 3 * N, c.s);
+  cudaMemsetAsync(c.status, 0, sizeof(int), c.s);
+  h->status = LBEH_OK;
+  h->steps = 0;
+  h->last_iters = 0;
+  h->last_relres = 0.0;
+  h->loaded = true;
+  const cudaError_t e = cudaGetLastError();
+  free_tmp(h, tmp);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return LBEH_ERR_CUDA;
+  return LBEH_OK;
+}
+
+int lbeh_step(lbeh_handle *h, int nsteps) {
+  if (!h || nsteps < 0) return LBEH_ERR_INVALID_ARG;
+  if (!h->loaded) return LBEH_ERR_INVALID_ARG;
+  Ctx &c = h->c;
+  for (int t = 0; t < nsteps; ++t) {
+    {
+      StageTimer st(h, LBEH_STAGE_MACRO);
+      h->ops.macro(c);
+      h->ops.virt(c);
+    }
+    if (h->pois) {
+      StageTimer st(h, LBEH_STAGE_POISSON);
+      double rr = 0.0;
+      const int it = poisson_solve(h->pois, c, h->p.poisson_tol, h->p.poisson_max_iter, &rr);
+      if (it == -1) return LBEH_ERR_CUDA;
+      h->last_relres = rr;
+      if (it < -1) {
+        h->last_iters = -it - 2;
+        h->status = LBEH_ERR_POISSON_NOT_CONVERGED;
+      } else {
+        h->last_iters = it;
+      }
+    }
+    {
+      StageTimer st(h, LBEH_STAGE_COLLIDE);
+      h->ops.collide(c);
+      c.cur ^= 1;
+    }
+    if (c.nions) {
+      StageTimer st(h, LBEH_STAGE_NP);
+      h->ops.np(c);
+      c.ncur ^= 1;
+    }
+    if (c.solids) {
+      StageTimer st(h, LBEH_STAGE_COLLOID);
+      h->ops.colloid_bb(c);
+    }
+    ++h->steps;
+  }
+  if (cudaGetLastError() != cudaSuccess) return LBEH_ERR_CUDA;
+  return h->status;
+}
+
+int lbeh_observables(lbeh_handle *h, lbeh_obs *out) {
+  if (!h || !out) return LBEH_ERR_INVALID_ARG;
+  Ctx &c = h->c;
+  std::memset(out, 0, sizeof(*out));
+  h->ops.obs_partials(c, c.red, kRedBlocks);
+  double *res = c.red + (size_t)kRedBlocks * kObsLen;
+  reduce_partials_final(c.red, kRedBlocks, kObsLen, res, c.s);
+  double v[kObsLen];
+  cudaMemcpyAsync(v, res, sizeof(v), cudaMemcpyDeviceToHost, c.s);
+  if (cudaStreamSynchronize(c.s) != cudaSuccess) return LBEH_ERR_CUDA;
+  out->mass[0] = v[0];
+  out->mass[1] = v[1];
+  out->ions[0] = v[2];
+  out->ions[1] = v[3];
+  out->charge = v[4];
+  for (int a = 0; a < 3; ++a) out->momentum[a] = v[5 + a];
+  if (v[8] > 0) {
+    const double W = v[8];
+    for (int a = 0; a < 3; ++a) out->centroid[a] = v[9 + a] / W;
+    const double mxx = v[12] - W * out->centroid[0] * out->centroid[0];
+    const double mzz = v[13] - W * out->centroid[2] * out->centroid[2];
+    const double a = std::sqrt(mxx > 0 ? mxx : 0), b = std::sqrt(mzz > 0 ? mzz : 0);
+    out->deformation = (a + b) > 0 ? (b - a) / (b + a) : 0.0;
+  }
+  if (c.ncoll) {
+    std::vector<double> cv(3 * c.ncoll);
+    cudaMemcpy(cv.data(), c.cv, 8 * 3 * c.ncoll, cudaMemcpyDeviceToHost);
+    for (int j = 0; j < c.ncoll; ++j)
+      for (int a = 0; a < 3; ++a) out->colloid_v[a] += cv[3 * j + a] / c.ncoll;
+  }
+  out->poisson_relres = h->last_relres;
+  out->poisson_iters = h->last_iters;
+  out->status = h->status;
+  out->steps = h->steps;
+  return LBEH_OK;
+}
+
+int lbeh_get_fields(lbeh_handle *h, lbeh_fields *out) {
+  if (!h || !out) return LBEH_ERR_INVALID_ARG;
+  if (out->dtype != LBEH_F64 && out->dtype != LBEH_F32) return LBEH_ERR_INVALID_ARG;
+  Ctx &c = h->c;
+  const long long N = c.d.N;
+  std::vector<void *> tmp;
+  bool ok = true;
+  if (out->rho[0] || out->rho[1]) {
+    double *rd = nullptr;
+    if (cudaMalloc(&rd, 8 * c.ncomp * N) != cudaSuccess) return LBEH_ERR_OOM;
+    tmp.push_back(rd);
+    h->ops.get_rho(c, rd);
+    for (int s = 0; s < c.ncomp; ++s)
+      if (out->rho[s]) ok &= stage_out(h, rd + s * N, out->rho[s], out->dtype, out->on_device, N, tmp);
+  }
+  if (out->f) {
+    double *fd = nullptr;
+    if (cudaMalloc(&fd, 8 * (size_t)c.ncomp * 19 * N) != cudaSuccess) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
+    tmp.push_back(fd);
+    h->ops.get_f(c, fd);
+    ok &= stage_out(h, fd, out->f, out->dtype, out->on_device, (long long)c.ncomp * 19 * N, tmp);
+  }
+  if (out->u) {
+    const double *ud = as_f64(h, c.u, 3 * N, tmp);
+    ok &= ud && stage_out(h, ud, out->u, out->dtype, out->on_device, 3 * N, tmp);
+  }
+  if (c.nions) {
+    const double *nd = as_f64(h, c.n[c.ncur], 2 * N, tmp);
+    for (int s = 0; s < 2; ++s)
+      if (out->n[s]) ok &= nd && stage_out(h, nd + s * N, out->n[s], out->dtype, out->on_device, N, tmp);
+  }
+  if (out->phi) ok &= stage_out(h, c.phi, out->phi, out->dtype, out->on_device, N, tmp);
+  const int nc = c.ncoll;
+  if (nc && (out->cx || out->cv || out->cf)) {
+    if (out->cx) cudaMemcpyAsync(out->cx, c.cx, 8 * 3 * nc, cudaMemcpyDeviceToHost, c.s);
+    if (out->cv) cudaMemcpyAsync(out->cv, c.cv, 8 * 3 * nc, cudaMemcpyDeviceToHost, c.s);
+    if (out->cf) cudaMemcpyAsync(out->cf, c.cforce, 8 * 3 * nc, cudaMemcpyDeviceToHost, c.s);
+  }
+  if (nc && out->cq) std::memcpy(out->cq, h->hq.data(), 8 * nc);
+  if (nc && out->cr) std::memcpy(out->cr, h->hr.data(), 8 * nc);
+  out->ncolloid = nc;
+  const cudaError_t e = cudaGetLastError();
+  free_tmp(h, tmp);
+  if (!ok || e != cudaSuccess) return LBEH_ERR_CUDA;
+  return LBEH_OK;
+}
+
+int lbeh_get_aux(lbeh_handle *h, int which, void *out_host) {
+  if (!h || !out_host) return LBEH_ERR_INVALID_ARG;
+  Ctx &c = h->c;
+  const long long N = c.d.N;
+  std::vector<void *> tmp;
+  bool ok = true;
+  switch (which) {
+    case LBEH_AUX_SOLID: ok = cuda_ok(cudaMemcpyAsync(out_host, c.solid, N, cudaMemcpyDeviceToHost, c.s)); break;
+    case LBEH_AUX_SURFACE:
+      ok = cuda_ok(cudaMemcpyAsync(out_host, c.surface, N, cudaMemcpyDeviceToHost, c.s));
+      break;
+    case LBEH_AUX_OWNER: ok = cuda_ok(cudaMemcpyAsync(out_host, c.owner, 4 * N, cudaMemcpyDeviceToHost, c.s)); break;
+    case LBEH_AUX_PSI_S:
+    case LBEH_AUX_QC:
+    case LBEH_AUX_EPS:
+    case LBEH_AUX_Q: {
+      void *src = which == LBEH_AUX_PSI_S ? c.psi_s : which == LBEH_AUX_QC ? c.qc : which == LBEH_AUX_EPS ? c.eps : c.q;
+      const double *d = as_f64(h, src, N, tmp);
+      ok = d && stage_out(h, d, out_host, LBEH_F64, 0, N, tmp);
+      break;
+    }
+    case LBEH_AUX_RHO_V: {
+      const double *d = as_f64(h, c.rho, (long long)c.ncomp * N, tmp);
+      ok = d && stage_out(h, d, out_host, LBEH_F64, 0, (long long)c.ncomp * N, tmp);
+      break;
+    }
+    case LBEH_AUX_U: {
+      const double *d = as_f64(h, c.u, 3 * N, tmp);
+      ok = d && stage_out(h, d, out_host, LBEH_F64, 0, 3 * N, tmp);
+      break;
+    }
+    default: return LBEH_ERR_INVALID_ARG;
+  }
+  const cudaError_t e = cudaGetLastError();
+  free_tmp(h, tmp);
+  return (ok && e == cudaSuccess) ? LBEH_OK : LBEH_ERR_CUDA;
+}
+
+}  // extern "C"

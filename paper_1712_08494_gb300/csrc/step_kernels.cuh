@@ -1,0 +1,774 @@
+// Kernels of the coupled lattice timestep, templated on the population
+// storage type S and the compute type T.  Included once per precision mode.
+//
+// Per step (Sec. II):
+//   k_macro    rho^sigma, psi^sigma = 1 - exp(-rho), eps(c, psi_s), q       (II.B, II.C, II.E)
+//   k_virtual  mean fluid density on interface solid nodes (Jansen)        (II.E)
+//   [Poisson]  phi from eps, q and the applied field                         (II.B, II.D)
+//   k_collide  E = -grad phi + E_ext, ion face fluxes, Shan-Chen fluid-fluid
+//              and fluid-ion forces, friction, Kelvin force, physical
+//              velocity, forced BGK collision (velocity shift), push
+//              streaming with halfway bounce-back and moving-wall term      (II.A-II.E)
+//   k_np       finite-volume Nernst-Planck update, upwind advection        (II.B)
+#pragma once
+
+#include "internal.h"
+
+namespace lbeh {
+
+template <typename T> __device__ __forceinline__ T expm1_t(T v);
+template <> __device__ __forceinline__ double expm1_t<double>(double v) { return expm1(v); }
+template <> __device__ __forceinline__ float expm1_t<float>(float v) { return expm1f(v); }
+
+template <typename T> struct StepK {
+  Dims d;
+  int ncomp, nions;
+  bool solids, has_field, solvation;
+  T tau, inv_tau, G, D, inv_2D;
+  T gas[2], dmd[2];
+  T eps_a, eps_b, eps_p, eps_bar;
+  T Eext[3];
+  T shift[2];
+};
+
+template <typename T> StepK<T> make_stepk(const Ctx &c) {
+  StepK<T> k;
+  k.d = c.d;
+  k.ncomp = c.ncomp;
+  k.nions = c.nions;
+  k.solids = c.solids;
+  k.has_field = c.has_field;
+  k.solvation = c.solvation;
+  k.tau = T(c.tau);
+  k.inv_tau = T(1.0 / c.tau);
+  k.G = T(c.G);
+  k.D = T(c.D);
+  k.inv_2D = c.D > 0 ? T(1.0 / (2.0 * c.D)) : T(0);
+  for (int s = 0; s < 2; ++s) {
+    k.gas[s] = T(c.gas[s]);
+    k.dmd[s] = T(c.dmd[s]);
+    k.shift[s] = T(c.shift[s]);
+  }
+  k.eps_a = T(c.eps_a);
+  k.eps_b = T(c.eps_b);
+  k.eps_p = T(c.eps_p);
+  k.eps_bar = T(c.eps_bar);
+  for (int a = 0; a < 3; ++a) k.Eext[a] = T(c.Eext[a]);
+  return k;
+}
+
+// eps = psi_s eps_p + (1 - psi_s) eps_f(c),  eps_f = [eps_a(1-c) + eps_b(1+c)]/2
+template <typename T>
+__device__ __forceinline__ T permittivity(const StepK<T> &k, T ra, T rb, T ps) {
+  T tot = ra + rb;
+  T c = tot > T(0) ? (rb - ra) / tot : T(0);
+  T ef = T(0.5) * (k.eps_a * (T(1) - c) + k.eps_b * (T(1) + c));
+  return ps * k.eps_p + (T(1) - ps) * ef;
+}
+
+// ---------------------------------------------------------------- k_macro
+template <typename S, typename T, int NC>
+__global__ void __launch_bounds__(256) k_macro(StepK<T> k, const S *__restrict__ f, T *__restrict__ rho,
+                                               T *__restrict__ psi, T *__restrict__ eps, T *__restrict__ q,
+                                               const T *__restrict__ n, const T *__restrict__ qc,
+                                               const T *__restrict__ psi_s, const uint8_t *__restrict__ solid) {
+  const long long N = k.d.N;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  T r[2] = {T(0), T(0)};
+  const bool sol = k.solids && solid[i];
+  if (!sol) {
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      T acc = T(0);
+#pragma unroll
+      for (int qd = 0; qd < 19; ++qd)
+        acc += Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]);
+      r[s] = acc;
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    rho[s * N + i] = r[s];
+    psi[s * N + i] = -expm1_t<T>(-r[s]);
+  }
+  T ps = k.solids ? psi_s[i] : T(0);
+  eps[i] = permittivity(k, r[0], NC == 2 ? r[1] : T(0), ps);
+  T qq = k.solids ? qc[i] : T(0);
+  if (k.nions) qq += n[i] - n[N + i];
+  q[i] = qq;
+}
+
+// ---------------------------------------------------------------- k_virtual
+// One block per colloid walks the colloid's bounding box; surface nodes get
+// the mean density of their fluid D3Q19 neighbours, and their psi and eps.
+template <typename T, int NC>
+__global__ void k_virtual(StepK<T> k, T *__restrict__ rho, T *__restrict__ psi, T *__restrict__ eps,
+                          const T *__restrict__ psi_s, const uint8_t *__restrict__ solid,
+                          const uint8_t *__restrict__ surface, const int *__restrict__ owner,
+                          const double *__restrict__ cx, const double *__restrict__ cr) {
+  const int j = blockIdx.x;
+  const Dims d = k.d;
+  const long long N = d.N;
+  int lo[3], cnt[3];
+  const int dims[3] = {d.nx, d.ny, d.nz};
+  for (int a = 0; a < 3; ++a) {
+    double X = cx[3 * j + a], r = cr[j];
+    lo[a] = int(ceil(X - r - 2.0));
+    int hi = int(floor(X + r + 2.0));
+    cnt[a] = min(dims[a], hi - lo[a] + 1);
+  }
+  const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
+  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+    int ox = int(t % cnt[0]);
+    int oy = int((t / cnt[0]) % cnt[1]);
+    int oz = int(t / ((long long)cnt[0] * cnt[1]));
+    int x = ((lo[0] + ox) % d.nx + d.nx) % d.nx;
+    int y = ((lo[1] + oy) % d.ny + d.ny) % d.ny;
+    int z = ((lo[2] + oz) % d.nz + d.nz) % d.nz;
+    long long i = site(d, x, y, z);
+    if (!surface[i] || owner[i] != j) continue;
+    long long nb[19];
+    neighbours19(d, x, y, z, nb);
+    T acc[2] = {T(0), T(0)};
+    int c = 0;
+#pragma unroll
+    for (int qd = 1; qd < 19; ++qd) {
+      if (!solid[nb[qd]]) {
+        ++c;
+#pragma unroll
+        for (int s = 0; s < NC; ++s) acc[s] += rho[s * N + nb[qd]];
+      }
+    }
+    T rv[2] = {T(0), T(0)};
+#pragma unroll
+    for (int s = 0; s < NC; ++s) {
+      rv[s] = c > 0 ? acc[s] / T(c) : T(0);
+      rho[s * N + i] = rv[s];
+      psi[s * N + i] = -expm1_t<T>(-rv[s]);
+    }
+    eps[i] = permittivity(k, rv[0], NC == 2 ? rv[1] : T(0), psi_s[i]);
+  }
+}
+
+// ---------------------------------------------------------------- k_collide
+template <typename S, typename T, int NC, bool SOL, bool IONS>
+__global__ void __launch_bounds__(256)
+    k_collide(StepK<T> k, const S *__restrict__ f, S *__restrict__ fn, const T *__restrict__ rhoF,
+              const T *__restrict__ psiF, const T *__restrict__ eps, const double *__restrict__ phi,
+              const T *__restrict__ n, const T *__restrict__ psi_f, const uint8_t *__restrict__ solid,
+              const int *__restrict__ owner, const double *__restrict__ cv, T *__restrict__ u_out,
+              T *__restrict__ flux_out) {
+  const Dims d = k.d;
+  const long long N = d.N;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  if (SOL && solid[i]) return;
+  int x, y, z;
+  coords(d, i, x, y, z);
+  long long nb[19];
+  neighbours19(d, x, y, z, nb);
+
+  // populations and moments
+  T fl[NC][19];
+  T rho[2] = {T(0), T(0)};
+  T J[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+#pragma unroll
+    for (int qd = 0; qd < 19; ++qd) {
+      T v = Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]);
+      fl[s][qd] = v;
+      rho[s] += v;
+    }
+  }
+#pragma unroll
+  for (int qd = 1; qd < 19; ++qd) {
+    T v = fl[0][qd];
+    if (NC == 2) v += fl[1][qd];
+    if (cx(qd)) J[0] += T(cx(qd)) * v;
+    if (cy(qd)) J[1] += T(cy(qd)) * v;
+    if (cz(qd)) J[2] += T(cz(qd)) * v;
+  }
+  const T rho_tot = rho[0] + (NC == 2 ? rho[1] : T(0));
+  const T inv_rho = rho_tot > T(0) ? T(1) / rho_tot : T(0);
+
+  T Phi[2][3] = {{T(0), T(0), T(0)}, {T(0), T(0), T(0)}};
+
+  // Shan-Chen fluid-fluid force (Sec. II.C eq. shanChenForce)
+  if (NC == 2 && k.G != T(0)) {
+    T Sa[3] = {T(0), T(0), T(0)}, Sb[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int qd = 1; qd < 19; ++qd) {
+      const T pa = wq<T>(qd) * psiF[nb[qd]];
+      const T pb = wq<T>(qd) * psiF[N + nb[qd]];
+      if (cx(qd)) { Sa[0] += T(cx(qd)) * pb; Sb[0] += T(cx(qd)) * pa; }
+      if (cy(qd)) { Sa[1] += T(cy(qd)) * pb; Sb[1] += T(cy(qd)) * pa; }
+      if (cz(qd)) { Sa[2] += T(cz(qd)) * pb; Sb[2] += T(cz(qd)) * pa; }
+    }
+    const T ga = -k.G * psiF[i], gb = -k.G * psiF[N + i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      Phi[0][a] += ga * Sa[a];
+      Phi[1][a] += gb * Sb[a];
+    }
+  }
+  // Shan-Chen fluid-ion (solvation) force on component a (Sec. II.C eq. solvation:force1)
+  if (IONS && k.solvation) {
+    T Si[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      if (k.gas[s] == T(0)) continue;
+      T acc[3] = {T(0), T(0), T(0)};
+#pragma unroll
+      for (int qd = 1; qd < 19; ++qd) {
+        const T v = wq<T>(qd) * n[s * N + nb[qd]];
+        if (cx(qd)) acc[0] += T(cx(qd)) * v;
+        if (cy(qd)) acc[1] += T(cy(qd)) * v;
+        if (cz(qd)) acc[2] += T(cz(qd)) * v;
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Si[a] += k.gas[s] * acc[a];
+    }
+    const T pa = psiF[i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Phi[0][a] += -pa * Si[a];
+  }
+
+  T Fel[3] = {T(0), T(0), T(0)};
+  if (k.has_field) {
+    // E = -grad phi + E_ext at i and its six axis neighbours
+    const double p0 = phi[i];
+    // axis neighbour indices: +x=1 -x=2 +y=3 -y=4 +z=5 -z=6
+    T Ei[3];
+    Ei[0] = T(-(phi[nb[1]] - phi[nb[2]]) * 0.5) + k.Eext[0];
+    Ei[1] = T(-(phi[nb[3]] - phi[nb[4]]) * 0.5) + k.Eext[1];
+    Ei[2] = T(-(phi[nb[5]] - phi[nb[6]]) * 0.5) + k.Eext[2];
+    // the distance-2 points along each axis
+    const long long p2[6] = {site(d, wrap(x + 2, d.nx), y, z), site(d, wrap(x - 2, d.nx), y, z),
+                             site(d, x, wrap(y + 2, d.ny), z), site(d, x, wrap(y - 2, d.ny), z),
+                             site(d, x, y, wrap(z + 2, d.nz)), site(d, x, y, wrap(z - 2, d.nz))};
+    // E components at the axis neighbours: Enb[dir][comp], dir = 0..5 (+x -x +y -y +z -z)
+    T Enb[6][3];
+    // along-axis components
+    Enb[0][0] = T(-(phi[p2[0]] - p0) * 0.5) + k.Eext[0];
+    Enb[1][0] = T(-(p0 - phi[p2[1]]) * 0.5) + k.Eext[0];
+    Enb[2][1] = T(-(phi[p2[2]] - p0) * 0.5) + k.Eext[1];
+    Enb[3][1] = T(-(p0 - phi[p2[3]]) * 0.5) + k.Eext[1];
+    Enb[4][2] = T(-(phi[p2[4]] - p0) * 0.5) + k.Eext[2];
+    Enb[5][2] = T(-(p0 - phi[p2[5]]) * 0.5) + k.Eext[2];
+    // transverse components from the face diagonals
+    // +x neighbour: y from (1,1,0)=7 and (1,-1,0)=9; z from (1,0,1)=11 and (1,0,-1)=13
+    Enb[0][1] = T(-(phi[nb[7]] - phi[nb[9]]) * 0.5) + k.Eext[1];
+    Enb[0][2] = T(-(phi[nb[11]] - phi[nb[13]]) * 0.5) + k.Eext[2];
+    // -x neighbour: y from (-1,1,0)=10 and (-1,-1,0)=8; z from (-1,0,1)=14 and (-1,0,-1)=12
+    Enb[1][1] = T(-(phi[nb[10]] - phi[nb[8]]) * 0.5) + k.Eext[1];
+    Enb[1][2] = T(-(phi[nb[14]] - phi[nb[12]]) * 0.5) + k.Eext[2];
+    // +y neighbour: x from (1,1,0)=7 and (-1,1,0)=10; z from (0,1,1)=15 and (0,1,-1)=17
+    Enb[2][0] = T(-(phi[nb[7]] - phi[nb[10]]) * 0.5) + k.Eext[0];
+    Enb[2][2] = T(-(phi[nb[15]] - phi[nb[17]]) * 0.5) + k.Eext[2];
+    // -y neighbour: x from (1,-1,0)=9 and (-1,-1,0)=8; z from (0,-1,1)=18 and (0,-1,-1)=16
+    Enb[3][0] = T(-(phi[nb[9]] - phi[nb[8]]) * 0.5) + k.Eext[0];
+    Enb[3][2] = T(-(phi[nb[18]] - phi[nb[16]]) * 0.5) + k.Eext[2];
+    // +z neighbour: x from (1,0,1)=11 and (-1,0,1)=14; y from (0,1,1)=15 and (0,-1,1)=18
+    Enb[4][0] = T(-(phi[nb[11]] - phi[nb[14]]) * 0.5) + k.Eext[0];
+    Enb[4][1] = T(-(phi[nb[15]] - phi[nb[18]]) * 0.5) + k.Eext[1];
+    // -z neighbour: x from (1,0,-1)=13 and (-1,0,-1)=12; y from (0,1,-1)=17 and (0,-1,-1)=16
+    Enb[5][0] = T(-(phi[nb[13]] - phi[nb[12]]) * 0.5) + k.Eext[0];
+    Enb[5][1] = T(-(phi[nb[17]] - phi[nb[16]]) * 0.5) + k.Eext[1];
+
+    // Kelvin force +(eps - eps_bar)/4 sum_{Q6} |E(i+d)|^2 c_d (Sec. II.C, discrete total force)
+    const T de = T(0.25) * (eps[i] - k.eps_bar);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const T e2p = Enb[2 * a][0] * Enb[2 * a][0] + Enb[2 * a][1] * Enb[2 * a][1] + Enb[2 * a][2] * Enb[2 * a][2];
+      const T e2m = Enb[2 * a + 1][0] * Enb[2 * a + 1][0] + Enb[2 * a + 1][1] * Enb[2 * a + 1][1] +
+                    Enb[2 * a + 1][2] * Enb[2 * a + 1][2];
+      Fel[a] = de * (e2p - e2m);
+    }
+
+    if (IONS) {
+      // face fluxes (Sec. II.B eq. ionic-fluxes-disc, Sec. II.E eq. ionic-fluxes-disc-2)
+      const T pf_i = SOL ? psi_f[i] : T(1);
+      T nt_i[2];
+#pragma unroll
+      for (int s = 0; s < 2; ++s) nt_i[s] = pf_i > T(0) ? n[s * N + i] / pf_i : T(0);
+      const T ra_i = rhoF[i];
+      T fric[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const long long jp = nb[1 + 2 * a], jm = nb[2 + 2 * a];
+        const T pf_p = SOL ? psi_f[jp] : T(1);
+        const T pf_m = SOL ? psi_f[jm] : T(1);
+        const T Ep = T(0.5) * (Ei[a] + Enb[2 * a][a]);
+        const T Em = T(0.5) * (Enb[2 * a + 1][a] + Ei[a]);
+        const T dr_p = rhoF[jp] - ra_i;
+        const T dr_m = ra_i - rhoF[jm];
+        const T wp = k.D * pf_i * pf_p;
+        const T wm = k.D * pf_m * pf_i;
+        T tot = T(0);
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          const T zs = s == 0 ? T(1) : T(-1);
+          const T ntp = pf_p > T(0) ? n[s * N + jp] / pf_p : T(0);
+          const T ntm = pf_m > T(0) ? n[s * N + jm] / pf_m : T(0);
+          const T nbp = T(0.5) * (nt_i[s] + ntp);
+          const T nbm = T(0.5) * (ntm + nt_i[s]);
+          const T Fp = wp * ((ntp - nt_i[s]) - zs * nbp * Ep - k.dmd[s] * nbp * dr_p);
+          const T Fm = wm * ((nt_i[s] - ntm) - zs * nbm * Em - k.dmd[s] * nbm * dr_m);
+          flux_out[(s * 3 + a) * N + i] = Fp;
+          tot += Fp + Fm;
+        }
+        fric[a] = -tot * k.inv_2D;  // friction (Sec. II.C eq. frictionforce), faces shared by two cells
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) Fel[a] += fric[a];
+    }
+  } else if (IONS) {
+    // no potential and no applied field: fluxes from diffusion and solvation only
+    const T pf_i = SOL ? psi_f[i] : T(1);
+    T nt_i[2];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) nt_i[s] = pf_i > T(0) ? n[s * N + i] / pf_i : T(0);
+    const T ra_i = rhoF[i];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long jp = nb[1 + 2 * a], jm = nb[2 + 2 * a];
+      const T pf_p = SOL ? psi_f[jp] : T(1);
+      const T pf_m = SOL ? psi_f[jm] : T(1);
+      const T dr_p = rhoF[jp] - ra_i;
+      const T dr_m = ra_i - rhoF[jm];
+      const T wp = k.D * pf_i * pf_p;
+      const T wm = k.D * pf_m * pf_i;
+      T tot = T(0);
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        const T ntp = pf_p > T(0) ? n[s * N + jp] / pf_p : T(0);
+        const T ntm = pf_m > T(0) ? n[s * N + jm] / pf_m : T(0);
+        const T nbp = T(0.5) * (nt_i[s] + ntp);
+        const T nbm = T(0.5) * (ntm + nt_i[s]);
+        const T Fp = wp * ((ntp - nt_i[s]) - k.dmd[s] * nbp * dr_p);
+        const T Fm = wm * ((nt_i[s] - ntm) - k.dmd[s] * nbm * dr_m);
+        flux_out[(s * 3 + a) * N + i] = Fp;
+        tot += Fp + Fm;
+      }
+      Fel[a] += -tot * k.inv_2D;
+    }
+  }
+
+  // electric and friction forces shared by mass fraction
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    const T fr = rho[s] * inv_rho;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Phi[s][a] += fr * Fel[a];
+  }
+  T ubar[3], uphys[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ubar[a] = J[a] * inv_rho;
+    T ps = Phi[0][a] + (NC == 2 ? Phi[1][a] : T(0));
+    uphys[a] = (J[a] + T(0.5) * ps) * inv_rho;
+    u_out[a * N + i] = uphys[a];
+  }
+
+  // forced BGK collision with the shifted equilibrium velocity, push streaming,
+  // halfway bounce-back on links to solid nodes (Sec. II.A, II.E)
+#pragma unroll
+  for (int s = 0; s < NC; ++s) {
+    T ue[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) ue[a] = rho[s] > T(0) ? ubar[a] + k.tau * Phi[s][a] / rho[s] : ubar[a];
+    const T usq = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
+    const T sh = k.shift[s];
+#pragma unroll
+    for (int qd = 0; qd < 19; ++qd) {
+      const T cu = T(cx(qd)) * ue[0] + T(cy(qd)) * ue[1] + T(cz(qd)) * ue[2];
+      const T feq = wq<T>(qd) * rho[s] * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
+      const T fpost = fl[s][qd] + (feq - fl[s][qd]) * k.inv_tau;
+      if (qd == 0) {
+        Store<S, T>::st(fn, (size_t)(s * 19) * N + i, fpost, wq<T>(0) * sh);
+      } else {
+        const long long jn = nb[qd];
+        if (SOL && solid[jn]) {
+          const int o = owner[jn];
+          const T cvd = T(double(cx(qd)) * cv[3 * o] + double(cy(qd)) * cv[3 * o + 1] +
+                          double(cz(qd)) * cv[3 * o + 2]);
+          const T val = fpost - T(6) * wq<T>(qd) * rho[s] * cvd;
+          Store<S, T>::st(fn, (size_t)(s * 19 + opp(qd)) * N + i, val, wq<T>(qd) * sh);
+        } else {
+          Store<S, T>::st(fn, (size_t)(s * 19 + qd) * N + jn, fpost, wq<T>(qd) * sh);
+        }
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- k_np
+template <typename T, bool SOL>
+__global__ void __launch_bounds__(256) k_np(StepK<T> k, const T *__restrict__ n, T *__restrict__ nn,
+                                            const T *__restrict__ flux, const T *__restrict__ u,
+                                            const uint8_t *__restrict__ solid) {
+  const Dims d = k.d;
+  const long long N = d.N;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  if (SOL && solid[i]) {
+    nn[i] = T(0);
+    nn[N + i] = T(0);
+    return;
+  }
+  int x, y, z;
+  coords(d, i, x, y, z);
+  const long long jm[3] = {site(d, wrapm(x, d.nx), y, z), site(d, x, wrapm(y, d.ny), z),
+                           site(d, x, y, wrapm(z, d.nz))};
+  const long long jp[3] = {site(d, wrapp(x, d.nx), y, z), site(d, x, wrapp(y, d.ny), z),
+                           site(d, x, y, wrapp(z, d.nz))};
+  bool okp[3], okm[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    okp[a] = !SOL || !solid[jp[a]];
+    okm[a] = !SOL || !solid[jm[a]];
+  }
+  T ui[3], up[3], um[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ui[a] = u[a * N + i];
+    um[a] = u[a * N + jm[a]];  // the cell upstream along +a
+    up[a] = u[a * N + jp[a]];  // the cell upstream along -a
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const T ni = n[s * N + i];
+    T div = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) div += flux[(s * 3 + a) * N + i] - flux[(s * 3 + a) * N + jm[a]];
+    T out = T(0), in = T(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      // +a: i sends max(u_a,0) n_i to i+a; i receives from i-a its max(u_a(i-a),0) n_{i-a}
+      if (okp[a]) out += fmax(ui[a], T(0)) * ni;
+      if (okm[a]) out += fmax(-ui[a], T(0)) * ni;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      if (okm[a]) in += fmax(um[a], T(0)) * n[s * N + jm[a]];
+      if (okp[a]) in += fmax(-up[a], T(0)) * n[s * N + jp[a]];
+    }
+    nn[s * N + i] = ((ni + div) - out) + in;
+  }
+}
+
+// ---------------------------------------------------------------- init / read-out
+template <typename S, typename T, int NC>
+__global__ void k_init_eq(StepK<T> k, S *__restrict__ f, const double *__restrict__ rho,
+                          const double *__restrict__ u, const uint8_t *__restrict__ solid) {
+  const long long N = k.d.N;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const bool sol = k.solids && solid[i];
+  double uu[3] = {0, 0, 0};
+  if (u) {
+    uu[0] = u[i];
+    uu[1] = u[N + i];
+    uu[2] = u[2 * N + i];
+  }
+  const double usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+  for (int s = 0; s < NC; ++s) {
+    const double r = sol ? 0.0 : rho[s * N + i];
+    for (int qd = 0; qd < 19; ++qd) {
+      const double cu = cx(qd) * uu[0] + cy(qd) * uu[1] + cz(qd) * uu[2];
+      const double feq = wq<double>(qd) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+      Store<S, T>::st(f, (size_t)(s * 19 + qd) * N + i, T(feq), wq<T>(qd) * k.shift[s]);
+    }
+  }
+}
+
+template <typename S, typename T, int NC>
+__global__ void k_init_f(StepK<T> k, S *__restrict__ f, const double *__restrict__ src,
+                         const uint8_t *__restrict__ solid) {
+  const long long N = k.d.N;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const bool sol = k.solids && solid[i];
+  for (int s = 0; s < NC; ++s)
+    for (int qd = 0; qd < 19; ++qd) {
+      size_t j = (size_t)(s * 19 + qd) * N + i;
+      Store<S, T>::st(f, j, sol ? T(0) : T(src[j]), wq<T>(qd) * k.shift[s]);
+    }
+}
+
+template <typename S, typename T, int NC>
+__global__ void k_get_f(StepK<T> k, const S *__restrict__ f, double *__restrict__ out,
+                        const uint8_t *__restrict__ solid) {
+  const long long N = k.d.N;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const bool sol = k.solids && solid[i];
+  for (int s = 0; s < NC; ++s)
+    for (int qd = 0; qd < 19; ++qd) {
+      size_t j = (size_t)(s * 19 + qd) * N + i;
+      out[j] = sol ? 0.0 : double(Store<S, T>::ld(f, j, wq<T>(qd) * k.shift[s]));
+    }
+}
+
+template <typename S, typename T, int NC>
+__global__ void k_get_rho(StepK<T> k, const S *__restrict__ f, double *__restrict__ out,
+                          const uint8_t *__restrict__ solid) {
+  const long long N = k.d.N;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const bool sol = k.solids && solid[i];
+  for (int s = 0; s < NC; ++s) {
+    T acc = T(0);
+    if (!sol)
+      for (int qd = 0; qd < 19; ++qd)
+        acc += Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]);
+    out[s * N + i] = double(acc);
+  }
+}
+
+// ---------------------------------------------------------------- observables
+// Per-block FP64 partial sums, fixed order (block-strided sites, then a tree).
+// Layout: 0,1 mass; 2,3 ions; 4 charge; 5..7 momentum; 8 W; 9..11 W x,y,z;
+// 12 W x^2; 13 W z^2; 14,15 unused.
+template <typename S, typename T, int NC>
+__global__ void __launch_bounds__(256) k_obs(StepK<T> k, const S *__restrict__ f, const T *__restrict__ n,
+                                             const T *__restrict__ qc, const uint8_t *__restrict__ solid,
+                                             double *__restrict__ partials) {
+  const Dims d = k.d;
+  const long long N = d.N;
+  double acc[kObsLen];
+#pragma unroll
+  for (int t = 0; t < kObsLen; ++t) acc[t] = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const bool sol = k.solids && solid[i];
+    if (k.nions) {
+      const double np = double(n[i]), nm = double(n[N + i]);
+      acc[2] += np;
+      acc[3] += nm;
+      acc[4] += np - nm;
+    }
+    if (k.solids) acc[4] += double(qc[i]);
+    if (sol) continue;
+    double r[2] = {0.0, 0.0}, J[3] = {0.0, 0.0, 0.0};
+    for (int s = 0; s < NC; ++s)
+      for (int qd = 0; qd < 19; ++qd) {
+        const double v = double(Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]));
+        r[s] += v;
+        J[0] += cx(qd) * v;
+        J[1] += cy(qd) * v;
+        J[2] += cz(qd) * v;
+      }
+    acc[0] += r[0];
+    acc[1] += r[1];
+    acc[5] += J[0];
+    acc[6] += J[1];
+    acc[7] += J[2];
+    if (NC == 2) {
+      const double tot = r[0] + r[1];
+      const double c = tot > 0 ? (r[1] - r[0]) / tot : 0.0;
+      const double w = c > 0 ? c : 0.0;
+      if (w > 0) {
+        int x, y, z;
+        coords(d, i, x, y, z);
+        acc[8] += w;
+        acc[9] += w * x;
+        acc[10] += w * y;
+        acc[11] += w * z;
+        acc[12] += w * double(x) * x;
+        acc[13] += w * double(z) * z;
+      }
+    }
+  }
+  __shared__ double sh[kObsLen][256];
+#pragma unroll
+  for (int t = 0; t < kObsLen; ++t) sh[t][threadIdx.x] = acc[t];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int t = 0; t < kObsLen; ++t) sh[t][threadIdx.x] += sh[t][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < kObsLen) partials[blockIdx.x * kObsLen + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// ---------------------------------------------------------------- colloid momentum exchange
+// One block per colloid: for fluid nodes of its bounding box and links to its
+// solid nodes, the momentum [2 f*_q - 6 w_q rho (c_q.v)] c_q with
+// f*_q = fn_{opp(q)} + 6 w_q rho (c_q.v) recovered from the bounced population.
+template <typename S, typename T, int NC>
+__global__ void k_colloid_bb(StepK<T> k, const S *__restrict__ fn, const T *__restrict__ rhoF,
+                             const uint8_t *__restrict__ solid, const int *__restrict__ owner,
+                             const double *__restrict__ ccx, const double *__restrict__ ccr,
+                             const double *__restrict__ cv, double *__restrict__ cforce) {
+  const int j = blockIdx.x;
+  const Dims d = k.d;
+  const long long N = d.N;
+  int lo[3], cnt[3];
+  const int dims[3] = {d.nx, d.ny, d.nz};
+  for (int a = 0; a < 3; ++a) {
+    double X = ccx[3 * j + a], r = ccr[j];
+    lo[a] = int(ceil(X - r - 2.0));
+    int hi = int(floor(X + r + 2.0));
+    cnt[a] = min(dims[a], hi - lo[a] + 1);
+  }
+  const double v[3] = {cv[3 * j], cv[3 * j + 1], cv[3 * j + 2]};
+  double acc[3] = {0, 0, 0};
+  const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
+  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+    int x = ((lo[0] + int(t % cnt[0])) % d.nx + d.nx) % d.nx;
+    int y = ((lo[1] + int((t / cnt[0]) % cnt[1])) % d.ny + d.ny) % d.ny;
+    int z = ((lo[2] + int(t / ((long long)cnt[0] * cnt[1]))) % d.nz + d.nz) % d.nz;
+    long long i = site(d, x, y, z);
+    if (solid[i]) continue;
+    long long nb[19];
+    neighbours19(d, x, y, z, nb);
+    for (int qd = 1; qd < 19; ++qd) {
+      if (!solid[nb[qd]] || owner[nb[qd]] != j) continue;
+      const double cvd = cx(qd) * v[0] + cy(qd) * v[1] + cz(qd) * v[2];
+      double dp = 0;
+      for (int s = 0; s < NC; ++s) {
+        const double r = double(rhoF[s * N + i]);
+        const double corr = 6.0 * wq<double>(qd) * r * cvd;
+        const double back = double(Store<S, T>::ld(fn, (size_t)(s * 19 + opp(qd)) * N + i,
+                                                   wq<T>(qd) * k.shift[s]));
+        dp += 2.0 * (back + corr) - corr;
+      }
+      acc[0] += cx(qd) * dp;
+      acc[1] += cy(qd) * dp;
+      acc[2] += cz(qd) * dp;
+    }
+  }
+  __shared__ double sh[3][256];
+  for (int a = 0; a < 3; ++a) sh[a][threadIdx.x] = acc[a];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int a = 0; a < 3; ++a) sh[a][threadIdx.x] += sh[a][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) cforce[3 * j + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// ---------------------------------------------------------------- host launchers
+template <typename S, typename T> struct Launch {
+  static constexpr int B = 256;
+
+  static void init_eq(Ctx &c, const double *rho, const double *u) {
+    auto k = make_stepk<T>(c);
+    S *f = (S *)c.f[c.cur];
+    if (c.ncomp == 2)
+      count_launch(), k_init_eq<S, T, 2><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, rho, u, c.solid);
+    else
+      count_launch(), k_init_eq<S, T, 1><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, rho, u, c.solid);
+  }
+  static void init_f(Ctx &c, const double *src) {
+    auto k = make_stepk<T>(c);
+    S *f = (S *)c.f[c.cur];
+    if (c.ncomp == 2)
+      count_launch(), k_init_f<S, T, 2><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, src, c.solid);
+    else
+      count_launch(), k_init_f<S, T, 1><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, src, c.solid);
+  }
+  static void get_f(Ctx &c, double *out) {
+    auto k = make_stepk<T>(c);
+    const S *f = (const S *)c.f[c.cur];
+    if (c.ncomp == 2)
+      count_launch(), k_get_f<S, T, 2><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, out, c.solid);
+    else
+      count_launch(), k_get_f<S, T, 1><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, out, c.solid);
+  }
+  static void get_rho(Ctx &c, double *out) {
+    auto k = make_stepk<T>(c);
+    const S *f = (const S *)c.f[c.cur];
+    if (c.ncomp == 2)
+      count_launch(), k_get_rho<S, T, 2><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, out, c.solid);
+    else
+      count_launch(), k_get_rho<S, T, 1><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, out, c.solid);
+  }
+  static void macro(Ctx &c) {
+    auto k = make_stepk<T>(c);
+    const S *f = (const S *)c.f[c.cur];
+    const T *n = (const T *)c.n[c.ncur];
+    if (c.ncomp == 2)
+      count_launch(), k_macro<S, T, 2><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, (T *)c.rho, (T *)c.psi, (T *)c.eps, (T *)c.q, n,
+                                                        (const T *)c.qc, (const T *)c.psi_s, c.solid);
+    else
+      count_launch(), k_macro<S, T, 1><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, (T *)c.rho, (T *)c.psi, (T *)c.eps, (T *)c.q, n,
+                                                        (const T *)c.qc, (const T *)c.psi_s, c.solid);
+  }
+  static void virt(Ctx &c) {
+    if (!c.solids || c.ncoll == 0) return;
+    auto k = make_stepk<T>(c);
+    if (c.ncomp == 2)
+      count_launch(), k_virtual<T, 2><<<c.ncoll, B, 0, c.s>>>(k, (T *)c.rho, (T *)c.psi, (T *)c.eps, (const T *)c.psi_s, c.solid,
+                                              c.surface, c.owner, c.cx, c.cr);
+    else
+      count_launch(), k_virtual<T, 1><<<c.ncoll, B, 0, c.s>>>(k, (T *)c.rho, (T *)c.psi, (T *)c.eps, (const T *)c.psi_s, c.solid,
+                                              c.surface, c.owner, c.cx, c.cr);
+  }
+  template <int NC, bool SOL, bool IONS> static void collide_v(Ctx &c) {
+    auto k = make_stepk<T>(c);
+    count_launch(), k_collide<S, T, NC, SOL, IONS><<<grid_for(c.d.N, B), B, 0, c.s>>>(
+        k, (const S *)c.f[c.cur], (S *)c.f[1 - c.cur], (const T *)c.rho, (const T *)c.psi, (const T *)c.eps, c.phi,
+        (const T *)c.n[c.ncur], (const T *)c.psi_f, c.solid, c.owner, c.cv, (T *)c.u, (T *)c.flux);
+  }
+  static void collide(Ctx &c) {
+    const bool ions = c.nions > 0;
+    if (c.ncomp == 2) {
+      if (c.solids) { ions ? collide_v<2, true, true>(c) : collide_v<2, true, false>(c); }
+      else { ions ? collide_v<2, false, true>(c) : collide_v<2, false, false>(c); }
+    } else {
+      if (c.solids) { ions ? collide_v<1, true, true>(c) : collide_v<1, true, false>(c); }
+      else { ions ? collide_v<1, false, true>(c) : collide_v<1, false, false>(c); }
+    }
+  }
+  static void np(Ctx &c) {
+    if (!c.nions) return;
+    auto k = make_stepk<T>(c);
+    const T *n = (const T *)c.n[c.ncur];
+    T *nn = (T *)c.n[1 - c.ncur];
+    if (c.solids)
+      count_launch(), k_np<T, true><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, n, nn, (const T *)c.flux, (const T *)c.u, c.solid);
+    else
+      count_launch(), k_np<T, false><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, n, nn, (const T *)c.flux, (const T *)c.u, c.solid);
+  }
+  static void obs_partials(Ctx &c, double *partials, int nblocks) {
+    auto k = make_stepk<T>(c);
+    const S *f = (const S *)c.f[c.cur];
+    if (c.ncomp == 2)
+      count_launch(), k_obs<S, T, 2><<<nblocks, B, 0, c.s>>>(k, f, (const T *)c.n[c.ncur], (const T *)c.qc, c.solid, partials);
+    else
+      count_launch(), k_obs<S, T, 1><<<nblocks, B, 0, c.s>>>(k, f, (const T *)c.n[c.ncur], (const T *)c.qc, c.solid, partials);
+  }
+  static void colloid_bb(Ctx &c) {
+    if (!c.solids || c.ncoll == 0) return;
+    auto k = make_stepk<T>(c);
+    const S *fn = (const S *)c.f[c.cur];
+    if (c.ncomp == 2)
+      count_launch(), k_colloid_bb<S, T, 2><<<c.ncoll, B, 0, c.s>>>(k, fn, (const T *)c.rho, c.solid, c.owner, c.cx, c.cr, c.cv,
+                                                    c.cforce);
+    else
+      count_launch(), k_colloid_bb<S, T, 1><<<c.ncoll, B, 0, c.s>>>(k, fn, (const T *)c.rho, c.solid, c.owner, c.cx, c.cr, c.cv,
+                                                    c.cforce);
+  }
+  static PrecOps ops() {
+    PrecOps o;
+    o.init_eq = init_eq;
+    o.init_f = init_f;
+    o.get_f = get_f;
+    o.get_rho = get_rho;
+    o.macro = macro;
+    o.virt = virt;
+    o.collide = collide;
+    o.np = np;
+    o.obs_partials = obs_partials;
+    o.colloid_bb = colloid_bb;
+    return o;
+  }
+};
+
+}  // namespace lbeh

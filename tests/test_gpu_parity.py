@@ -1,0 +1,185 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 CPU oracle.
+
+Tolerances (max |gpu - oracle| / max |oracle| per field):
+  * FP64 path: 1e-11 after a few steps (round-off of different summation
+    orders, amplified by the nonlinear Shan-Chen coupling), with the Poisson
+    solves of both sides driven to a relative residual of 1e-13.
+  * FP32 compute and storage: 2e-5 (single-precision rounding, 24 bits,
+    accumulated over the steps).
+  * BF16 / FP16 shifted storage: 5e-3 / 1e-3 for the densities (the stored
+    deviation f - w rho0 keeps 8 / 11 mantissa bits).
+Bit-exact: solid mask, owner ids, solid fraction, surface nodes, surface charge.
+"""
+import numpy as np
+import pytest
+
+import synth
+from _common import compare, gpu_for, oracle_for, rel_err, step_both, with_params
+from oracle import geometry
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbeh():
+    import paper_1712_08494_gb300 as pkg
+    pkg.build()
+    from paper_1712_08494_gb300 import lbeh as L
+    return L
+
+
+def _slab(n=(20, 24, 28), G=4.0, prec="fp64", tol=1e-13, **kw):
+    nx, ny, nz = n
+    w = synth.two_slab(nx=nx, ny=ny, nz=nz, G=G, prec=prec, tol=tol, **kw)
+    w.colloid_x[:] = [[nx / 2.0, ny / 2.0, nz / 2.0 - 0.5]] if len(w.colloid_r) else w.colloid_x
+    return w
+
+
+# ---------------------------------------------------------------- geometry
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_geometry_bit_exact(lbeh, prec):
+    w = _slab(prec=prec)
+    # several colloids, one wrapping the periodic boundary, radius not integer
+    w.colloid_x = np.array([[10.0, 12.0, 13.5], [1.3, 22.9, 3.25], [15.6, 4.1, 24.7]])
+    w.colloid_r = np.array([4.0, 3.3, 2.7])
+    w.colloid_q = np.array([-20.0, 7.0, -3.0])
+    w.colloid_v = np.zeros((3, 3))
+    w.params.ncolloid_max = 3
+    sg = gpu_for(w, lbeh)
+    p = w.params
+    solid, owner, psi_s = geometry.project(p.nx, p.ny, p.nz, w.colloid_x, w.colloid_r, 3)
+    surf = geometry.surface_nodes(solid)
+    qc = geometry.colloid_charge(owner, surf, w.colloid_q)
+    assert np.array_equal(sg.aux(lbeh.LBEH_AUX_SOLID).astype(bool), solid)
+    assert np.array_equal(sg.aux(lbeh.LBEH_AUX_OWNER), owner.astype(np.int32))
+    assert np.array_equal(sg.aux(lbeh.LBEH_AUX_SURFACE).astype(bool), surf)
+    assert np.array_equal(sg.aux(lbeh.LBEH_AUX_PSI_S), psi_s)
+    q = sg.aux(lbeh.LBEH_AUX_QC)
+    if prec == "fp64":
+        assert np.array_equal(q, qc)
+    else:
+        assert np.array_equal(q, qc.astype(np.float32).astype(np.float64))
+    sg.close()
+
+
+# ---------------------------------------------------------------- FP64 path
+@pytest.mark.parametrize("G", [0.08, 4.0])
+def test_fp64_two_slab_with_colloid(lbeh, G):
+    w = _slab(G=G)
+    so = oracle_for(w)
+    sg = gpu_for(w, lbeh)
+    step_both(sg, so, 3)
+    errs = compare(sg, so)
+    assert all(e < 1e-11 for e in errs.values()), errs
+    # intermediate fields of the last step
+    assert rel_err(sg.aux(lbeh.LBEH_AUX_EPS), so.last_eps) < 1e-13
+    assert rel_err(sg.aux(lbeh.LBEH_AUX_RHO_V), so.last_rho_v) < 1e-12
+    o = sg.observables()
+    assert abs(o.charge) < 1e-10
+    sg.close()
+
+
+def test_fp64_droplet_field_solvation(lbeh):
+    """Applied field (dielectric polarisation), solvation forces, charged drop."""
+    w = synth.droplet(n=24, r=7.0, prec="fp64", tol=1e-13, Ez=0.02, charge=5.0, salt=2e-3)
+    w.params.dmu = (1.5, -0.5)
+    so = oracle_for(w)
+    sg = gpu_for(w, lbeh)
+    step_both(sg, so, 4)
+    errs = compare(sg, so)
+    assert all(e < 1e-11 for e in errs.values()), errs
+    sg.close()
+
+
+def test_fp64_single_component_fixed_colloids(lbeh):
+    w = synth.suspension(n=24, ncoll=3, r=3.0, prec="fp64", tol=1e-13, Ex=0.01)
+    w.params.colloids_move = 0
+    w.params.poisson_max_iter = 400   # eps_p/eps_a = 1/8: oracle split contracts by 0.78
+    w.params.ncolloid_max = 3
+    so = oracle_for(w)
+    sg = gpu_for(w, lbeh)
+    step_both(sg, so, 3)
+    errs = compare(sg, so)
+    assert all(e < 1e-11 for e in errs.values()), errs
+    cf = sg.get(("rho",))["cf"]
+    # momentum exchange of the last step vs the oracle's bounce-back sum
+    assert rel_err(cf, so.p_bb) < 1e-9
+    sg.close()
+
+
+def test_fp64_ion_free_no_poisson(lbeh):
+    w = synth.droplet(n=16, r=5.0, prec="fp64", nions=0, Ez=0.0)
+    so = oracle_for(w)
+    sg = gpu_for(w, lbeh)
+    step_both(sg, so, 5)
+    errs = compare(sg, so, ("rho", "u"))
+    assert all(e < 1e-12 for e in errs.values()), errs
+    sg.close()
+
+
+# ---------------------------------------------------------------- reduced precision
+@pytest.mark.parametrize("prec,tol_rho", [("fp32", 2e-5), ("bf16", 5e-3), ("fp16", 1e-3)])
+def test_reduced_precision_droplet(lbeh, prec, tol_rho):
+    w = synth.droplet(n=24, r=7.0, prec=prec, tol=1e-10, Ez=0.02, charge=5.0, salt=2e-3)
+    so = oracle_for(w)
+    sg = gpu_for(w, lbeh)
+    step_both(sg, so, 5)
+    errs = compare(sg, so, ("rho", "n", "phi"))
+    assert errs["rho"] < tol_rho, errs
+    assert errs["n"] < (2e-5 if prec == "fp32" else 10 * tol_rho), errs
+    assert errs["phi"] < (2e-4 if prec == "fp32" else 50 * tol_rho), errs
+    sg.close()
+
+
+def test_fp32_two_slab_with_colloid(lbeh):
+    w = _slab(prec="fp32", tol=1e-10)
+    so = oracle_for(w)
+    sg = gpu_for(w, lbeh)
+    step_both(sg, so, 4)
+    errs = compare(sg, so, ("rho", "n", "phi"))
+    assert errs["rho"] < 2e-5 and errs["n"] < 2e-5 and errs["phi"] < 2e-4, errs
+    sg.close()
+
+
+# ---------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("n", [(2, 2, 2), (4, 6, 2), (3, 5, 7)])
+def test_tiny_and_odd_boxes(lbeh, n):
+    nx, ny, nz = n
+    rng = np.random.default_rng(11)
+    p = synth.Params(nx=nx, ny=ny, nz=nz, ncomp=2, nions=2, prec="fp64", G=4.0, poisson_tol=1e-13,
+                     poisson_max_iter=400, E_ext=(0.01, 0.0, 0.02))
+    rho = rng.uniform(0.04, 0.7, size=(2, nz, ny, nx))
+    ions = rng.uniform(0.005, 0.015, size=(2, nz, ny, nx))
+    w = synth.Workload("tiny", p, rho, ions)
+    so = oracle_for(w)
+    sg = gpu_for(w, lbeh)
+    step_both(sg, so, 3)
+    errs = compare(sg, so)
+    assert all(e < 1e-11 for e in errs.values()), errs
+    sg.close()
+
+
+def test_poisson_cap_reports_status_not_fault(lbeh):
+    w = _slab(n=(16, 16, 16), tol=1e-14)
+    w.params.poisson_max_iter = 1
+    sg = gpu_for(w, lbeh)
+    rc = sg.step(1)
+    assert rc == lbeh.LBEH_ERR_POISSON_NOT_CONVERGED
+    assert sg.observables().status == lbeh.LBEH_ERR_POISSON_NOT_CONVERGED
+    # the handle stays usable and a fresh load clears the status
+    sg.set_fields(rho=list(w.rho), n=list(w.n), colloid_x=w.colloid_x, colloid_v=w.colloid_v,
+                  colloid_q=w.colloid_q, colloid_r=w.colloid_r)
+    assert sg.observables().status == lbeh.LBEH_OK
+    sg.close()
+
+
+def test_bitwise_reproducible(lbeh):
+    w = synth.droplet(n=24, r=7.0, prec="fp32", tol=1e-8, Ez=0.02, charge=5.0)
+    outs = []
+    for rep in range(2):
+        sg = gpu_for(w, lbeh)
+        sg.step(5)
+        outs.append(sg.get(("rho", "n", "phi")))
+        sg.close()
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
