@@ -34,7 +34,9 @@ LBEH_AUX_QC, LBEH_AUX_EPS, LBEH_AUX_Q, LBEH_AUX_RHO_V, LBEH_AUX_U = 4, 5, 6, 7, 
 
 # exported symbols declared in include/lbeh.h
 SYMBOLS = ("lbeh_create", "lbeh_set_fields", "lbeh_get_fields", "lbeh_step", "lbeh_observables",
-           "lbeh_get_aux", "lbeh_profile_enable", "lbeh_profile_read", "lbeh_destroy", "lbeh_status_string")
+           "lbeh_get_aux", "lbeh_profile_enable", "lbeh_profile_read", "lbeh_observables_noalloc",
+           "lbeh_destroy", "lbeh_status_string")
+LBEH_NOALLOC_MAX_SITES = 16777216
 
 LBEH_STAGE_MACRO, LBEH_STAGE_POISSON, LBEH_STAGE_COLLIDE, LBEH_STAGE_NP, LBEH_STAGE_COLLOID = 0, 1, 2, 3, 4
 LBEH_NSTAGES = 5
@@ -93,12 +95,14 @@ def _load():
     lib.lbeh_get_aux.argtypes = [H, C.c_int, C.c_void_p]
     lib.lbeh_profile_enable.argtypes = [H, C.c_int]
     lib.lbeh_profile_read.argtypes = [H, C.POINTER(lbeh_profile)]
+    lib.lbeh_observables_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                                             C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(lbeh_obs), C.c_void_p]
     lib.lbeh_destroy.argtypes = [H]
     lib.lbeh_destroy.restype = None
     lib.lbeh_status_string.argtypes = [C.c_int]
     lib.lbeh_status_string.restype = C.c_char_p
     for name in ("lbeh_create", "lbeh_set_fields", "lbeh_get_fields", "lbeh_step", "lbeh_observables",
-                 "lbeh_get_aux", "lbeh_profile_enable", "lbeh_profile_read"):
+                 "lbeh_get_aux", "lbeh_profile_enable", "lbeh_profile_read", "lbeh_observables_noalloc"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -166,6 +170,17 @@ def lbeh_profile_read(h) -> lbeh_profile:
     p = lbeh_profile()
     _check(_lib.lbeh_profile_read(h, C.byref(p)), "lbeh_profile_read")
     return p
+
+
+def lbeh_observables_noalloc(nx, ny, nz, ncomp, nions, dtype, f_ptr, n_ptr=None, solid_ptr=None, qc_ptr=None,
+                             stream=0) -> lbeh_obs:
+    """Allocation-free observables over caller-owned device buffers (pointers
+    as integers); for callers that cannot allocate device memory."""
+    o = lbeh_obs()
+    _check(_lib.lbeh_observables_noalloc(int(nx), int(ny), int(nz), int(ncomp), int(nions), int(dtype), f_ptr,
+                                         n_ptr, solid_ptr, qc_ptr, C.byref(o), int(stream) or None),
+           "lbeh_observables_noalloc")
+    return o
 
 
 def lbeh_destroy(h) -> None:
