@@ -34,10 +34,11 @@ sys.path.insert(0, ROOT)
 METRIC = "coupled-step MLUPS & % HBM roofline; BF16 vs FP32 speedup at stated error"
 SIZE = 128
 # algorithmic bytes per site of one k_collide launch (two components, two ion
-# species, no colloids): populations read+write, psi_a psi_b, rho_a, eps, phi
-# (FP64), n+ n-, written u and three face fluxes per species
-COLLIDE_BYTES = {"fp32": 2 * 19 * 4 * 2 + 8 + 4 + 4 + 8 + 8 + 12 + 24,
-                 "bf16": 2 * 19 * 2 * 2 + 8 + 4 + 4 + 8 + 8 + 12 + 24}
+# species, no colloids): populations read + written, then rho_a rho_b, J (3),
+# psi_a psi_b, eps, phi (compute-type copy) and n+ n- read once, u (3) and
+# the three owned face fluxes per species written
+_FIELDS = (2 + 3 + 2 + 1 + 1 + 2) * 4 + (3 + 6) * 4
+COLLIDE_BYTES = {"fp32": 2 * 19 * 4 * 2 + _FIELDS, "bf16": 2 * 19 * 2 * 2 + _FIELDS}
 
 
 def env_rank():
@@ -224,7 +225,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        sysg.profile_enable(True)
+        sysg.profile_enable(False)  # reset the launch counter; whole-step graphs stay on
         smp = ClockSampler(local) if prec == "fp32" else None
         if smp:
             smp.__enter__()
@@ -238,9 +239,17 @@ def run_ours(args):
         barrier()
         torch.cuda.synchronize()
         ms = max_over_ranks(e0.elapsed_time(e1))
-        prof = sysg.profile_read()
+        pr0 = sysg.profile_read()
+        launches, cycles = pr0["launches"], pr0["poisson_cycles"]
         obs = sysg.observables()
-        results[prec] = {"ms": ms, "prof": prof, "rc": rc, "obs": obs}
+        # per-kernel device times: CUDA events recorded by the library around
+        # each stage on the stream it launches on (eager launches, same kernels)
+        sysg.profile_enable(True)
+        sysg.step(min(args.steps, 100))
+        prof = sysg.profile_read()
+        sysg.profile_enable(False)
+        prof["launches"] = launches
+        results[prec] = {"ms": ms, "prof": prof, "rc": rc, "obs": obs, "cycles": cycles}
         fields[prec] = sysg.get(("rho",))["rho"]
         sysg.close()
         del sysg
@@ -306,7 +315,7 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": COLLIDE_BYTES["fp32"] * N,
                      "avg_launch_ms": t_coll * 1e3},
         "stage_share": {k: (v / total_ms if total_ms else None) for k, v in prof["ms"].items()},
-        "poisson_iters_last": results["fp32"]["obs"].poisson_iters,
+        "poisson_cycles_per_step": results["fp32"]["cycles"] / args.steps,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": prof["launches"],
     }
     print(json.dumps(line), flush=True)

@@ -178,6 +178,7 @@ typedef struct lbeh_profile {
   double ms[LBEH_NSTAGES];       /* summed device time per stage */
   long long calls[LBEH_NSTAGES]; /* stage executions */
   long long launches;            /* kernels launched by the library */
+  long long poisson_cycles;      /* multigrid cycles of the Poisson solves */
 } lbeh_profile;
 int lbeh_profile_enable(lbeh_handle *h, int on);
 int lbeh_profile_read(lbeh_handle *h, lbeh_profile *out);

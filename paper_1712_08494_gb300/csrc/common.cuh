@@ -81,12 +81,15 @@ __device__ __forceinline__ long long site(const Dims &d, int x, int y, int z) {
   return ((long long)z * d.ny + y) * d.nx + x;
 }
 
-// Grid-stride decomposition of a linear site index.
+// Decomposition of a linear site index (boxes hold fewer than 2^31 sites, so
+// 32-bit unsigned division suffices; 64-bit division is emulated and slow).
 __device__ __forceinline__ void coords(const Dims &d, long long i, int &x, int &y, int &z) {
-  long long r = i / d.nx;
-  x = int(i - r * d.nx);
-  z = int(r / d.ny);
-  y = int(r - (long long)z * d.ny);
+  const unsigned ii = unsigned(i);
+  const unsigned r = ii / unsigned(d.nx);
+  x = int(ii - r * unsigned(d.nx));
+  const unsigned zz = r / unsigned(d.ny);
+  z = int(zz);
+  y = int(r - zz * unsigned(d.ny));
 }
 
 // Device status word bits (sticky until lbeh_set_fields).

@@ -45,6 +45,8 @@ struct Ctx {
   void *psi_f = nullptr;   // [N]
   void *qc = nullptr;      // [N]
   double *phi = nullptr;   // [N]
+  void *phit = nullptr;    // [N] potential in the compute type (aliases phi in FP64)
+  void *J = nullptr;       // [3][N] momentum sum_sigma sum_q f c_q
   uint8_t *solid = nullptr, *surface = nullptr;
   int *owner = nullptr;
 
@@ -86,10 +88,24 @@ void geometry_build(Ctx &c);  // solid, owner, psi_s, psi_f, surface, ccount, qc
 
 // Poisson (poisson.cu).
 struct Poisson;
+struct PoissonStats {
+  int iters = 0;             // cycles of the last solve
+  double relres = 0.0;       // relative residual of the last solve
+  long long total_iters = 0; // cycles since creation
+  int notconv = 0;           // last solve hit the cycle cap
+  int body_launches = 0;     // kernels per cycle inside a captured graph
+};
 Poisson *poisson_create(const Ctx &c, int fp64);
 void poisson_destroy(Poisson *p);
-// Solves for c.phi from c.eps, c.q; returns iterations (negative on CUDA error).
-int poisson_solve(Poisson *p, Ctx &c, double tol, int max_iter, double *relres);
+int poisson_configure(Poisson *p, double tol, int max_iter, cudaStream_t s);
+int poisson_reset(Poisson *p, cudaStream_t s);  // new state: no previous solution to extrapolate from
+// Eager solve for c.phi from c.eps and c.q: returns the cycle count, -(count+2)
+// if the cap was reached before the tolerance, -1 on a CUDA error.
+int poisson_solve(Poisson *p, Ctx &c, double *relres);
+// Records the solve into the graph being captured on c.s, its cycles under a
+// conditional WHILE node driven by `handle`.  Returns 0 or -1.
+int poisson_capture(Poisson *p, Ctx &c, cudaGraphConditionalHandle handle);
+int poisson_read(Poisson *p, cudaStream_t s, PoissonStats *out);
 
 // Deterministic FP64 reductions (reduce.cu).
 void reduce_partials_final(const double *partials, int nblocks, int len, double *out, cudaStream_t s);

@@ -5,6 +5,7 @@
 // virtual densities, Poisson solve, fused forces/fluxes/collision/streaming
 // with bounce-back, Nernst-Planck update, colloid momentum exchange.
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -36,6 +37,15 @@ struct lbeh_handle {
   double prof_ms[LBEH_NSTAGES] = {0};
   long long prof_calls[LBEH_NSTAGES] = {0};
   long long launches0 = 0;
+  long long cycles0 = 0;
+  // whole-step CUDA graphs, one per ping-pong parity
+  cudaStream_t gs = nullptr;           // capture / replay stream
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  bool graphs_ready = false;
+  bool eager = false;                  // LBEH_EAGER=1 disables graphs
+  int graph_launches = 0;              // kernels per replay outside the Poisson cycles
+  long long total_iters_seen = 0;      // Poisson cycles already accounted
 };
 
 std::atomic<long long> lbeh::g_launches{0};
@@ -179,6 +189,7 @@ void free_tmp(lbeh_handle *h, std::vector<void *> &tmp) {
 int check_params(const lbeh_params *p) {
   if (!p) return LBEH_ERR_INVALID_ARG;
   if (p->nx < 2 || p->ny < 2 || p->nz < 2) return LBEH_ERR_INVALID_ARG;
+  if ((long long)p->nx * p->ny * p->nz >= (1LL << 31)) return LBEH_ERR_INVALID_ARG;  // 32-bit site indices
   if (p->ncomp != 1 && p->ncomp != 2) return LBEH_ERR_INVALID_ARG;
   if (p->nions != 0 && p->nions != 2) return LBEH_ERR_INVALID_ARG;
   if (p->prec < LBEH_FP64 || p->prec > LBEH_FP32_FP16STORE) return LBEH_ERR_INVALID_ARG;
@@ -188,6 +199,100 @@ int check_params(const lbeh_params *p) {
   if (p->nions && (p->dmu[0] != 0.0 || p->dmu[1] != 0.0) && p->drho_a == 0.0) return LBEH_ERR_INVALID_ARG;
   if (p->ncolloid_max < 0 || p->psi_subdiv < 0 || p->psi_subdiv > 15) return LBEH_ERR_INVALID_ARG;
   if (p->poisson_max_iter < 0) return LBEH_ERR_INVALID_ARG;
+  return LBEH_OK;
+}
+
+void drop_graphs(lbeh_handle *h) {
+  for (int k = 0; k < 2; ++k)
+    if (h->exec[k]) {
+      cudaGraphExecDestroy(h->exec[k]);
+      h->exec[k] = nullptr;
+    }
+  h->graphs_ready = false;
+}
+
+// Kernels of one coupled step on the context's stream (eager or captured).
+// `handle` != 0: the Poisson cycles go under a conditional WHILE node.
+int enqueue_step(lbeh_handle *h, Ctx &c, bool capture, cudaGraphConditionalHandle handle) {
+  {
+    StageTimer st(h, LBEH_STAGE_MACRO);
+    h->ops.macro(c);
+    h->ops.virt(c);
+  }
+  if (h->pois) {
+    StageTimer st(h, LBEH_STAGE_POISSON);
+    if (capture) {
+      if (poisson_capture(h->pois, c, handle) != 0) return LBEH_ERR_CUDA;
+    } else {
+      double rr = 0.0;
+      const int it = poisson_solve(h->pois, c, &rr);
+      if (it == -1) return LBEH_ERR_CUDA;
+      h->last_relres = rr;
+      if (it < -1) {
+        h->last_iters = -it - 2;
+        h->status = LBEH_ERR_POISSON_NOT_CONVERGED;
+      } else {
+        h->last_iters = it;
+      }
+    }
+  }
+  {
+    StageTimer st(h, LBEH_STAGE_COLLIDE);
+    h->ops.collide(c);
+    c.cur ^= 1;
+  }
+  if (c.nions) {
+    StageTimer st(h, LBEH_STAGE_NP);
+    h->ops.np(c);
+    c.ncur ^= 1;
+  }
+  if (c.solids) {
+    StageTimer st(h, LBEH_STAGE_COLLOID);
+    h->ops.colloid_bb(c);
+  }
+  return LBEH_OK;
+}
+
+// Capture the step for both ping-pong parities into graphs on h->gs.
+int build_graphs(lbeh_handle *h) {
+  drop_graphs(h);
+  const bool prof = h->prof;
+  h->prof = false;
+  int rc = LBEH_OK;
+  for (int par = 0; par < 2 && rc == LBEH_OK; ++par) {
+    Ctx cc = h->c;
+    cc.s = h->gs;
+    cc.cur = par;
+    cc.ncur = cc.nions ? par : 0;
+    const long long before = g_launches.load();
+    if (cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = LBEH_ERR_CUDA;
+      break;
+    }
+    cudaGraphConditionalHandle handle = 0;
+    if (h->pois) {
+      cudaStreamCaptureStatus cs;
+      cudaGraph_t g = nullptr;
+      if (cudaStreamGetCaptureInfo(h->gs, &cs, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess ||
+          cudaGraphConditionalHandleCreate(&handle, g, 0, 0) != cudaSuccess)
+        rc = LBEH_ERR_CUDA;
+    }
+    if (rc == LBEH_OK) rc = enqueue_step(h, cc, true, handle);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->gs, &graph);
+    h->graph_launches = int(g_launches.load() - before);
+    g_launches.fetch_sub(h->graph_launches);  // captured, not launched
+    if (rc == LBEH_OK && e != cudaSuccess) rc = LBEH_ERR_CUDA;
+    if (rc == LBEH_OK && cudaGraphInstantiate(&h->exec[par], graph, 0) != cudaSuccess) rc = LBEH_ERR_CUDA;
+    if (graph) cudaGraphDestroy(graph);
+  }
+  h->prof = prof;
+  if (rc != LBEH_OK) {
+    drop_graphs(h);
+    cudaGetLastError();
+    return rc;
+  }
+  h->graphs_ready = true;
   return LBEH_OK;
 }
 
@@ -260,6 +365,11 @@ int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
   ok &= (c.q = dalloc(h, T * N)) != nullptr;
   ok &= (c.u = dalloc(h, T * 3 * N)) != nullptr;
   ok &= (c.phi = (double *)dalloc(h, 8 * N)) != nullptr;
+  if (p->prec == LBEH_FP64)
+    c.phit = c.phi;
+  else
+    ok &= (c.phit = dalloc(h, 4 * N)) != nullptr;
+  ok &= (c.J = dalloc(h, T * 3 * N)) != nullptr;
   ok &= (c.psi_s = dalloc(h, T * N)) != nullptr;
   ok &= (c.psi_f = dalloc(h, T * N)) != nullptr;
   ok &= (c.qc = dalloc(h, T * N)) != nullptr;
@@ -284,6 +394,14 @@ int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
   if (ok && c.has_field) {
     h->pois = poisson_create(c, p->prec == LBEH_FP64);
     ok &= h->pois != nullptr;
+    if (h->pois) ok &= poisson_configure(h->pois, p->poisson_tol, p->poisson_max_iter, c.s) == 0;
+  }
+  ok &= cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking) == cudaSuccess;
+  ok &= cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) == cudaSuccess;
+  ok &= cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) == cudaSuccess;
+  {
+    const char *e = getenv("LBEH_EAGER");
+    h->eager = e && e[0] == '1';
   }
   if (!ok) {
     lbeh_destroy(h);
@@ -291,6 +409,7 @@ int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
   }
   cudaMemsetAsync(c.u, 0, T * 3 * N, c.s);
   cudaMemsetAsync(c.phi, 0, 8 * N, c.s);
+  if (c.phit != c.phi) cudaMemsetAsync(c.phit, 0, 4 * N, c.s);
   cudaMemsetAsync(c.status, 0, sizeof(int), c.s);
   cudaMemsetAsync(c.cv, 0, 8 * 3 * nc, c.s);
   cudaMemsetAsync(c.cforce, 0, 8 * 3 * nc, c.s);
@@ -316,6 +435,7 @@ int lbeh_profile_enable(lbeh_handle *h, int on) {
   }
   h->prof = on != 0;
   h->launches0 = g_launches.load();
+  h->cycles0 = h->total_iters_seen;
   return LBEH_OK;
 }
 
@@ -327,6 +447,7 @@ int lbeh_profile_read(lbeh_handle *h, lbeh_profile *out) {
     out->calls[k] = h->prof_calls[k];
   }
   out->launches = g_launches.load() - h->launches0;
+  out->poisson_cycles = h->total_iters_seen - h->cycles0;
   return cudaGetLastError() == cudaSuccess ? LBEH_OK : LBEH_ERR_CUDA;
 }
 
@@ -335,6 +456,13 @@ void lbeh_destroy(lbeh_handle *h) {
   if (h->c.s) cudaStreamSynchronize(h->c.s);
   flush_marks(h);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  drop_graphs(h);
+  if (h->gs) {
+    cudaStreamSynchronize(h->gs);
+    cudaStreamDestroy(h->gs);
+  }
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
   poisson_destroy(h->pois);
   for (void *a : h->allocs) cudaFree(a);
   delete h;
@@ -368,6 +496,7 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
     h->hr[j] = in->cr[j];
     if (!(h->hr[j] > 0.0)) return LBEH_ERR_INVALID_ARG;
   }
+  drop_graphs(h);
   c.ncoll = nc;
   c.solids = nc > 0;
   if (nc) {
@@ -425,8 +554,13 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
   } else {
     cudaMemsetAsync(c.phi, 0, 8 * N, c.s);
   }
+  if (c.phit != c.phi) to_compute(h, c.phi, c.phit, N);
   cudaMemsetAsync(c.u, 0, (c.prec == LBEH_FP64 ? 8 : 4) * 3 * N, c.s);
   cudaMemsetAsync(c.status, 0, sizeof(int), c.s);
+  if (h->pois && poisson_reset(h->pois, c.s) != 0) {
+    free_tmp(h, tmp);
+    return LBEH_ERR_CUDA;
+  }
   h->status = LBEH_OK;
   h->steps = 0;
   h->last_iters = 0;
@@ -442,40 +576,45 @@ int lbeh_step(lbeh_handle *h, int nsteps) {
   if (!h || nsteps < 0) return LBEH_ERR_INVALID_ARG;
   if (!h->loaded) return LBEH_ERR_INVALID_ARG;
   Ctx &c = h->c;
-  for (int t = 0; t < nsteps; ++t) {
-    {
-      StageTimer st(h, LBEH_STAGE_MACRO);
-      h->ops.macro(c);
-      h->ops.virt(c);
+  if (nsteps == 0) return h->status;
+  const bool graph = !h->eager && !h->prof;
+  if (graph) {
+    if (!h->graphs_ready) {
+      int rc = build_graphs(h);
+      if (rc != LBEH_OK) return rc;
     }
-    if (h->pois) {
-      StageTimer st(h, LBEH_STAGE_POISSON);
-      double rr = 0.0;
-      const int it = poisson_solve(h->pois, c, h->p.poisson_tol, h->p.poisson_max_iter, &rr);
-      if (it == -1) return LBEH_ERR_CUDA;
-      h->last_relres = rr;
-      if (it < -1) {
-        h->last_iters = -it - 2;
-        h->status = LBEH_ERR_POISSON_NOT_CONVERGED;
-      } else {
-        h->last_iters = it;
-      }
-    }
-    {
-      StageTimer st(h, LBEH_STAGE_COLLIDE);
-      h->ops.collide(c);
+    // replay on the capture stream, ordered after and before the caller's stream
+    cudaEventRecord(h->ev_in, c.s);
+    cudaStreamWaitEvent(h->gs, h->ev_in, 0);
+    for (int t = 0; t < nsteps; ++t) {
+      if (cudaGraphLaunch(h->exec[c.cur], h->gs) != cudaSuccess) return LBEH_ERR_CUDA;
+      g_launches.fetch_add(h->graph_launches);
       c.cur ^= 1;
+      if (c.nions) c.ncur ^= 1;
+      ++h->steps;
     }
-    if (c.nions) {
-      StageTimer st(h, LBEH_STAGE_NP);
-      h->ops.np(c);
-      c.ncur ^= 1;
+    cudaEventRecord(h->ev_out, h->gs);
+    cudaStreamWaitEvent(c.s, h->ev_out, 0);
+  } else {
+    for (int t = 0; t < nsteps; ++t) {
+      int rc = enqueue_step(h, c, false, 0);
+      if (rc != LBEH_OK) return rc;
+      ++h->steps;
     }
-    if (c.solids) {
-      StageTimer st(h, LBEH_STAGE_COLLOID);
-      h->ops.colloid_bb(c);
+  }
+  if (h->pois) {
+    PoissonStats ps;
+    if (poisson_read(h->pois, graph ? h->gs : c.s, &ps) != 0) return LBEH_ERR_CUDA;
+    if (cudaStreamSynchronize(c.s) != cudaSuccess) return LBEH_ERR_CUDA;
+    if (graph) {
+      g_launches.fetch_add((ps.total_iters - h->total_iters_seen) * ps.body_launches);
+      h->last_iters = ps.iters;
+      h->last_relres = ps.relres;
     }
-    ++h->steps;
+    h->total_iters_seen = ps.total_iters;
+    int dst = 0;
+    cudaMemcpy(&dst, c.status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (dst & ST_POISSON) h->status = LBEH_ERR_POISSON_NOT_CONVERGED;
   }
   if (cudaGetLastError() != cudaSuccess) return LBEH_ERR_CUDA;
   return h->status;

@@ -79,15 +79,19 @@ __global__ void __launch_bounds__(kNABlock)
     }
     if (qc) acc[4] += qc[i];
     if (solid && solid[i]) continue;
-    double r[2] = {0.0, 0.0}, J[3] = {0.0, 0.0, 0.0};
+    // per-site sums in the input's own precision, as the handle's reduction does
+    F rt[2] = {F(0), F(0)}, Jt[3] = {F(0), F(0), F(0)};
     for (int s = 0; s < ncomp; ++s)
+#pragma unroll
       for (int q = 0; q < 19; ++q) {
-        const double v = double(f[(size_t)(s * 19 + q) * N + i]);
-        r[s] += v;
-        J[0] += cx(q) * v;
-        J[1] += cy(q) * v;
-        J[2] += cz(q) * v;
+        const F v = f[(size_t)(s * 19 + q) * N + i];
+        rt[s] += v;
+        if (cx(q)) Jt[0] += F(cx(q)) * v;
+        if (cy(q)) Jt[1] += F(cy(q)) * v;
+        if (cz(q)) Jt[2] += F(cz(q)) * v;
       }
+    const double r[2] = {double(rt[0]), double(rt[1])};
+    const double J[3] = {double(Jt[0]), double(Jt[1]), double(Jt[2])};
     acc[0] += r[0];
     acc[1] += r[1];
     acc[5] += J[0];

@@ -69,24 +69,41 @@ __device__ __forceinline__ T permittivity(const StepK<T> &k, T ra, T rb, T ps) {
 // ---------------------------------------------------------------- k_macro
 template <typename S, typename T, int NC>
 __global__ void __launch_bounds__(256) k_macro(StepK<T> k, const S *__restrict__ f, T *__restrict__ rho,
-                                               T *__restrict__ psi, T *__restrict__ eps, T *__restrict__ q,
-                                               const T *__restrict__ n, const T *__restrict__ qc,
-                                               const T *__restrict__ psi_s, const uint8_t *__restrict__ solid) {
+                                               T *__restrict__ Jout, T *__restrict__ psi, T *__restrict__ eps,
+                                               T *__restrict__ q, const T *__restrict__ n,
+                                               const T *__restrict__ qc, const T *__restrict__ psi_s,
+                                               const uint8_t *__restrict__ solid) {
   const long long N = k.d.N;
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= N) return;
   T r[2] = {T(0), T(0)};
+  T J[3] = {T(0), T(0), T(0)};
   const bool sol = k.solids && solid[i];
   if (!sol) {
+    T fl[NC][19];
 #pragma unroll
     for (int s = 0; s < NC; ++s) {
       T acc = T(0);
 #pragma unroll
-      for (int qd = 0; qd < 19; ++qd)
-        acc += Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]);
+      for (int qd = 0; qd < 19; ++qd) {
+        fl[s][qd] = Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]);
+        acc += fl[s][qd];
+      }
       r[s] = acc;
     }
+    // momentum sum_sigma sum_q f c_q (equal relaxation times: one barycentric velocity)
+#pragma unroll
+    for (int qd = 1; qd < 19; ++qd) {
+      T v = fl[0][qd];
+      if (NC == 2) v += fl[1][qd];
+      if (cx(qd)) J[0] += T(cx(qd)) * v;
+      if (cy(qd)) J[1] += T(cy(qd)) * v;
+      if (cz(qd)) J[2] += T(cz(qd)) * v;
+    }
   }
+  Jout[i] = J[0];
+  Jout[N + i] = J[1];
+  Jout[2 * N + i] = J[2];
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
     rho[s * N + i] = r[s];
@@ -152,44 +169,41 @@ __global__ void k_virtual(StepK<T> k, T *__restrict__ rho, T *__restrict__ psi, 
 }
 
 // ---------------------------------------------------------------- k_collide
+// Forces and ion fluxes are formed first from the macro fields written by
+// k_macro (no population is live), then each component's populations are
+// loaded, relaxed and pushed.  Keeping the populations out of the force
+// phase holds the register footprint low enough for several resident blocks
+// per SM.  Site indices are 32-bit (boxes below 2^31 sites).
 template <typename S, typename T, int NC, bool SOL, bool IONS>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
     k_collide(StepK<T> k, const S *__restrict__ f, S *__restrict__ fn, const T *__restrict__ rhoF,
-              const T *__restrict__ psiF, const T *__restrict__ eps, const double *__restrict__ phi,
-              const T *__restrict__ n, const T *__restrict__ psi_f, const uint8_t *__restrict__ solid,
-              const int *__restrict__ owner, const double *__restrict__ cv, T *__restrict__ u_out,
-              T *__restrict__ flux_out) {
-  const Dims d = k.d;
-  const long long N = d.N;
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+              const T *__restrict__ JF, const T *__restrict__ psiF, const T *__restrict__ eps,
+              const T *__restrict__ phi, const T *__restrict__ n, const T *__restrict__ psi_f,
+              const uint8_t *__restrict__ solid, const int *__restrict__ owner, const double *__restrict__ cv,
+              T *__restrict__ u_out, T *__restrict__ flux_out) {
+  const int nx = k.d.nx, ny = k.d.ny, nz = k.d.nz;
+  const int N = int(k.d.N);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   if (SOL && solid[i]) return;
-  int x, y, z;
-  coords(d, i, x, y, z);
-  long long nb[19];
-  neighbours19(d, x, y, z, nb);
+  const int r = i / nx;
+  const int x = i - r * nx;
+  const int z = r / ny;
+  const int y = r - z * ny;
+  const int nxy = nx * ny;
+  // periodic neighbour offsets along each axis
+  const int oxm = (x == 0 ? nx - 1 : -1), oxp = (x + 1 == nx ? 1 - nx : 1);
+  const int oym = (y == 0 ? (ny - 1) * nx : -nx), oyp = (y + 1 == ny ? (1 - ny) * nx : nx);
+  const int ozm = (z == 0 ? (nz - 1) * nxy : -nxy), ozp = (z + 1 == nz ? (1 - nz) * nxy : nxy);
+  auto NB = [&](int q) -> int {
+    return i + (cx(q) < 0 ? oxm : (cx(q) > 0 ? oxp : 0)) + (cy(q) < 0 ? oym : (cy(q) > 0 ? oyp : 0)) +
+           (cz(q) < 0 ? ozm : (cz(q) > 0 ? ozp : 0));
+  };
 
-  // populations and moments
-  T fl[NC][19];
-  T rho[2] = {T(0), T(0)};
-  T J[3] = {T(0), T(0), T(0)};
-#pragma unroll
-  for (int s = 0; s < NC; ++s) {
-#pragma unroll
-    for (int qd = 0; qd < 19; ++qd) {
-      T v = Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]);
-      fl[s][qd] = v;
-      rho[s] += v;
-    }
-  }
-#pragma unroll
-  for (int qd = 1; qd < 19; ++qd) {
-    T v = fl[0][qd];
-    if (NC == 2) v += fl[1][qd];
-    if (cx(qd)) J[0] += T(cx(qd)) * v;
-    if (cy(qd)) J[1] += T(cy(qd)) * v;
-    if (cz(qd)) J[2] += T(cz(qd)) * v;
-  }
+  T rho[2];
+  rho[0] = rhoF[i];
+  rho[1] = NC == 2 ? rhoF[N + i] : T(0);
+  const T J[3] = {JF[i], JF[N + i], JF[2 * N + i]};
   const T rho_tot = rho[0] + (NC == 2 ? rho[1] : T(0));
   const T inv_rho = rho_tot > T(0) ? T(1) / rho_tot : T(0);
 
@@ -200,8 +214,9 @@ __global__ void __launch_bounds__(256)
     T Sa[3] = {T(0), T(0), T(0)}, Sb[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int qd = 1; qd < 19; ++qd) {
-      const T pa = wq<T>(qd) * psiF[nb[qd]];
-      const T pb = wq<T>(qd) * psiF[N + nb[qd]];
+      const int j = NB(qd);
+      const T pa = wq<T>(qd) * psiF[j];
+      const T pb = wq<T>(qd) * psiF[N + j];
       if (cx(qd)) { Sa[0] += T(cx(qd)) * pb; Sb[0] += T(cx(qd)) * pa; }
       if (cy(qd)) { Sa[1] += T(cy(qd)) * pb; Sb[1] += T(cy(qd)) * pa; }
       if (cz(qd)) { Sa[2] += T(cz(qd)) * pb; Sb[2] += T(cz(qd)) * pa; }
@@ -222,7 +237,7 @@ __global__ void __launch_bounds__(256)
       T acc[3] = {T(0), T(0), T(0)};
 #pragma unroll
       for (int qd = 1; qd < 19; ++qd) {
-        const T v = wq<T>(qd) * n[s * N + nb[qd]];
+        const T v = wq<T>(qd) * n[s * N + NB(qd)];
         if (cx(qd)) acc[0] += T(cx(qd)) * v;
         if (cy(qd)) acc[1] += T(cy(qd)) * v;
         if (cz(qd)) acc[2] += T(cz(qd)) * v;
@@ -236,46 +251,39 @@ __global__ void __launch_bounds__(256)
   }
 
   T Fel[3] = {T(0), T(0), T(0)};
+  // axis neighbours in the order +x -x +y -y +z -z
+  const int ax[6] = {i + oxp, i + oxm, i + oyp, i + oym, i + ozp, i + ozm};
   if (k.has_field) {
-    // E = -grad phi + E_ext at i and its six axis neighbours
-    const double p0 = phi[i];
-    // axis neighbour indices: +x=1 -x=2 +y=3 -y=4 +z=5 -z=6
+    // E = -grad phi + E_ext at i and at its six axis neighbours
+    const T p0 = phi[i];
     T Ei[3];
-    Ei[0] = T(-(phi[nb[1]] - phi[nb[2]]) * 0.5) + k.Eext[0];
-    Ei[1] = T(-(phi[nb[3]] - phi[nb[4]]) * 0.5) + k.Eext[1];
-    Ei[2] = T(-(phi[nb[5]] - phi[nb[6]]) * 0.5) + k.Eext[2];
-    // the distance-2 points along each axis
-    const long long p2[6] = {site(d, wrap(x + 2, d.nx), y, z), site(d, wrap(x - 2, d.nx), y, z),
-                             site(d, x, wrap(y + 2, d.ny), z), site(d, x, wrap(y - 2, d.ny), z),
-                             site(d, x, y, wrap(z + 2, d.nz)), site(d, x, y, wrap(z - 2, d.nz))};
-    // E components at the axis neighbours: Enb[dir][comp], dir = 0..5 (+x -x +y -y +z -z)
+    Ei[0] = T(-0.5) * (phi[ax[0]] - phi[ax[1]]) + k.Eext[0];
+    Ei[1] = T(-0.5) * (phi[ax[2]] - phi[ax[3]]) + k.Eext[1];
+    Ei[2] = T(-0.5) * (phi[ax[4]] - phi[ax[5]]) + k.Eext[2];
+    // Enb[dir][comp]: along-axis components use the distance-2 points, the
+    // transverse ones the face diagonals
+    const int x2p = x + 2 >= nx ? x + 2 - nx : x + 2, x2m = x - 2 < 0 ? x - 2 + nx : x - 2;
+    const int y2p = y + 2 >= ny ? y + 2 - ny : y + 2, y2m = y - 2 < 0 ? y - 2 + ny : y - 2;
+    const int z2p = z + 2 >= nz ? z + 2 - nz : z + 2, z2m = z - 2 < 0 ? z - 2 + nz : z - 2;
     T Enb[6][3];
-    // along-axis components
-    Enb[0][0] = T(-(phi[p2[0]] - p0) * 0.5) + k.Eext[0];
-    Enb[1][0] = T(-(p0 - phi[p2[1]]) * 0.5) + k.Eext[0];
-    Enb[2][1] = T(-(phi[p2[2]] - p0) * 0.5) + k.Eext[1];
-    Enb[3][1] = T(-(p0 - phi[p2[3]]) * 0.5) + k.Eext[1];
-    Enb[4][2] = T(-(phi[p2[4]] - p0) * 0.5) + k.Eext[2];
-    Enb[5][2] = T(-(p0 - phi[p2[5]]) * 0.5) + k.Eext[2];
-    // transverse components from the face diagonals
-    // +x neighbour: y from (1,1,0)=7 and (1,-1,0)=9; z from (1,0,1)=11 and (1,0,-1)=13
-    Enb[0][1] = T(-(phi[nb[7]] - phi[nb[9]]) * 0.5) + k.Eext[1];
-    Enb[0][2] = T(-(phi[nb[11]] - phi[nb[13]]) * 0.5) + k.Eext[2];
-    // -x neighbour: y from (-1,1,0)=10 and (-1,-1,0)=8; z from (-1,0,1)=14 and (-1,0,-1)=12
-    Enb[1][1] = T(-(phi[nb[10]] - phi[nb[8]]) * 0.5) + k.Eext[1];
-    Enb[1][2] = T(-(phi[nb[14]] - phi[nb[12]]) * 0.5) + k.Eext[2];
-    // +y neighbour: x from (1,1,0)=7 and (-1,1,0)=10; z from (0,1,1)=15 and (0,1,-1)=17
-    Enb[2][0] = T(-(phi[nb[7]] - phi[nb[10]]) * 0.5) + k.Eext[0];
-    Enb[2][2] = T(-(phi[nb[15]] - phi[nb[17]]) * 0.5) + k.Eext[2];
-    // -y neighbour: x from (1,-1,0)=9 and (-1,-1,0)=8; z from (0,-1,1)=18 and (0,-1,-1)=16
-    Enb[3][0] = T(-(phi[nb[9]] - phi[nb[8]]) * 0.5) + k.Eext[0];
-    Enb[3][2] = T(-(phi[nb[18]] - phi[nb[16]]) * 0.5) + k.Eext[2];
-    // +z neighbour: x from (1,0,1)=11 and (-1,0,1)=14; y from (0,1,1)=15 and (0,-1,1)=18
-    Enb[4][0] = T(-(phi[nb[11]] - phi[nb[14]]) * 0.5) + k.Eext[0];
-    Enb[4][1] = T(-(phi[nb[15]] - phi[nb[18]]) * 0.5) + k.Eext[1];
-    // -z neighbour: x from (1,0,-1)=13 and (-1,0,-1)=12; y from (0,1,-1)=17 and (0,-1,-1)=16
-    Enb[5][0] = T(-(phi[nb[13]] - phi[nb[12]]) * 0.5) + k.Eext[0];
-    Enb[5][1] = T(-(phi[nb[17]] - phi[nb[16]]) * 0.5) + k.Eext[1];
+    Enb[0][0] = T(-0.5) * (phi[i - x + x2p] - p0) + k.Eext[0];
+    Enb[1][0] = T(-0.5) * (p0 - phi[i - x + x2m]) + k.Eext[0];
+    Enb[2][1] = T(-0.5) * (phi[i + (y2p - y) * nx] - p0) + k.Eext[1];
+    Enb[3][1] = T(-0.5) * (p0 - phi[i + (y2m - y) * nx]) + k.Eext[1];
+    Enb[4][2] = T(-0.5) * (phi[i + (z2p - z) * nxy] - p0) + k.Eext[2];
+    Enb[5][2] = T(-0.5) * (p0 - phi[i + (z2m - z) * nxy]) + k.Eext[2];
+    Enb[0][1] = T(-0.5) * (phi[NB(7)] - phi[NB(9)]) + k.Eext[1];
+    Enb[0][2] = T(-0.5) * (phi[NB(11)] - phi[NB(13)]) + k.Eext[2];
+    Enb[1][1] = T(-0.5) * (phi[NB(10)] - phi[NB(8)]) + k.Eext[1];
+    Enb[1][2] = T(-0.5) * (phi[NB(14)] - phi[NB(12)]) + k.Eext[2];
+    Enb[2][0] = T(-0.5) * (phi[NB(7)] - phi[NB(10)]) + k.Eext[0];
+    Enb[2][2] = T(-0.5) * (phi[NB(15)] - phi[NB(17)]) + k.Eext[2];
+    Enb[3][0] = T(-0.5) * (phi[NB(9)] - phi[NB(8)]) + k.Eext[0];
+    Enb[3][2] = T(-0.5) * (phi[NB(18)] - phi[NB(16)]) + k.Eext[2];
+    Enb[4][0] = T(-0.5) * (phi[NB(11)] - phi[NB(14)]) + k.Eext[0];
+    Enb[4][1] = T(-0.5) * (phi[NB(15)] - phi[NB(18)]) + k.Eext[1];
+    Enb[5][0] = T(-0.5) * (phi[NB(13)] - phi[NB(12)]) + k.Eext[0];
+    Enb[5][1] = T(-0.5) * (phi[NB(17)] - phi[NB(16)]) + k.Eext[1];
 
     // Kelvin force +(eps - eps_bar)/4 sum_{Q6} |E(i+d)|^2 c_d (Sec. II.C, discrete total force)
     const T de = T(0.25) * (eps[i] - k.eps_bar);
@@ -286,18 +294,16 @@ __global__ void __launch_bounds__(256)
                     Enb[2 * a + 1][2] * Enb[2 * a + 1][2];
       Fel[a] = de * (e2p - e2m);
     }
-
     if (IONS) {
       // face fluxes (Sec. II.B eq. ionic-fluxes-disc, Sec. II.E eq. ionic-fluxes-disc-2)
       const T pf_i = SOL ? psi_f[i] : T(1);
       T nt_i[2];
 #pragma unroll
       for (int s = 0; s < 2; ++s) nt_i[s] = pf_i > T(0) ? n[s * N + i] / pf_i : T(0);
-      const T ra_i = rhoF[i];
-      T fric[3];
+      const T ra_i = rho[0];
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        const long long jp = nb[1 + 2 * a], jm = nb[2 + 2 * a];
+        const int jp = ax[2 * a], jm = ax[2 * a + 1];
         const T pf_p = SOL ? psi_f[jp] : T(1);
         const T pf_m = SOL ? psi_f[jm] : T(1);
         const T Ep = T(0.5) * (Ei[a] + Enb[2 * a][a]);
@@ -319,21 +325,19 @@ __global__ void __launch_bounds__(256)
           flux_out[(s * 3 + a) * N + i] = Fp;
           tot += Fp + Fm;
         }
-        fric[a] = -tot * k.inv_2D;  // friction (Sec. II.C eq. frictionforce), faces shared by two cells
+        Fel[a] += -tot * k.inv_2D;  // friction (Sec. II.C eq. frictionforce), faces shared by two cells
       }
-#pragma unroll
-      for (int a = 0; a < 3; ++a) Fel[a] += fric[a];
     }
   } else if (IONS) {
-    // no potential and no applied field: fluxes from diffusion and solvation only
+    // no potential and no applied field: diffusion and solvation fluxes only
     const T pf_i = SOL ? psi_f[i] : T(1);
     T nt_i[2];
 #pragma unroll
     for (int s = 0; s < 2; ++s) nt_i[s] = pf_i > T(0) ? n[s * N + i] / pf_i : T(0);
-    const T ra_i = rhoF[i];
+    const T ra_i = rho[0];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const long long jp = nb[1 + 2 * a], jm = nb[2 + 2 * a];
+      const int jp = ax[2 * a], jm = ax[2 * a + 1];
       const T pf_p = SOL ? psi_f[jp] : T(1);
       const T pf_m = SOL ? psi_f[jm] : T(1);
       const T dr_p = rhoF[jp] - ra_i;
@@ -363,41 +367,44 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int a = 0; a < 3; ++a) Phi[s][a] += fr * Fel[a];
   }
-  T ubar[3], uphys[3];
+  T ue[2][3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    ubar[a] = J[a] * inv_rho;
-    T ps = Phi[0][a] + (NC == 2 ? Phi[1][a] : T(0));
-    uphys[a] = (J[a] + T(0.5) * ps) * inv_rho;
-    u_out[a * N + i] = uphys[a];
+    const T ubar = J[a] * inv_rho;
+    const T ps = Phi[0][a] + (NC == 2 ? Phi[1][a] : T(0));
+    u_out[a * N + i] = (J[a] + T(0.5) * ps) * inv_rho;
+#pragma unroll
+    for (int s = 0; s < NC; ++s) ue[s][a] = rho[s] > T(0) ? ubar + k.tau * Phi[s][a] / rho[s] : ubar;
   }
 
   // forced BGK collision with the shifted equilibrium velocity, push streaming,
   // halfway bounce-back on links to solid nodes (Sec. II.A, II.E)
 #pragma unroll
   for (int s = 0; s < NC; ++s) {
-    T ue[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) ue[a] = rho[s] > T(0) ? ubar[a] + k.tau * Phi[s][a] / rho[s] : ubar[a];
-    const T usq = ue[0] * ue[0] + ue[1] * ue[1] + ue[2] * ue[2];
+    const S *fs = f + (size_t)(s * 19) * N;
+    S *fns = fn + (size_t)(s * 19) * N;
     const T sh = k.shift[s];
+    T fl[19];
+#pragma unroll
+    for (int qd = 0; qd < 19; ++qd) fl[qd] = Store<S, T>::ld(fs, (size_t)qd * N + i, wq<T>(qd) * sh);
+    const T usq = ue[s][0] * ue[s][0] + ue[s][1] * ue[s][1] + ue[s][2] * ue[s][2];
 #pragma unroll
     for (int qd = 0; qd < 19; ++qd) {
-      const T cu = T(cx(qd)) * ue[0] + T(cy(qd)) * ue[1] + T(cz(qd)) * ue[2];
+      const T cu = T(cx(qd)) * ue[s][0] + T(cy(qd)) * ue[s][1] + T(cz(qd)) * ue[s][2];
       const T feq = wq<T>(qd) * rho[s] * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
-      const T fpost = fl[s][qd] + (feq - fl[s][qd]) * k.inv_tau;
+      const T fpost = fl[qd] + (feq - fl[qd]) * k.inv_tau;
       if (qd == 0) {
-        Store<S, T>::st(fn, (size_t)(s * 19) * N + i, fpost, wq<T>(0) * sh);
+        Store<S, T>::st(fns, (size_t)i, fpost, wq<T>(0) * sh);
       } else {
-        const long long jn = nb[qd];
+        const int jn = NB(qd);
         if (SOL && solid[jn]) {
           const int o = owner[jn];
           const T cvd = T(double(cx(qd)) * cv[3 * o] + double(cy(qd)) * cv[3 * o + 1] +
                           double(cz(qd)) * cv[3 * o + 2]);
           const T val = fpost - T(6) * wq<T>(qd) * rho[s] * cvd;
-          Store<S, T>::st(fn, (size_t)(s * 19 + opp(qd)) * N + i, val, wq<T>(qd) * sh);
+          Store<S, T>::st(fns, (size_t)opp(qd) * N + i, val, wq<T>(qd) * sh);
         } else {
-          Store<S, T>::st(fn, (size_t)(s * 19 + qd) * N + jn, fpost, wq<T>(qd) * sh);
+          Store<S, T>::st(fns, (size_t)qd * N + jn, fpost, wq<T>(qd) * sh);
         }
       }
     }
@@ -467,19 +474,21 @@ __global__ void k_init_eq(StepK<T> k, S *__restrict__ f, const double *__restric
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= N) return;
   const bool sol = k.solids && solid[i];
-  double uu[3] = {0, 0, 0};
+  T uu[3] = {T(0), T(0), T(0)};
   if (u) {
-    uu[0] = u[i];
-    uu[1] = u[N + i];
-    uu[2] = u[2 * N + i];
+    uu[0] = T(u[i]);
+    uu[1] = T(u[N + i]);
+    uu[2] = T(u[2 * N + i]);
   }
-  const double usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+  const T usq = uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2];
+#pragma unroll
   for (int s = 0; s < NC; ++s) {
-    const double r = sol ? 0.0 : rho[s * N + i];
+    const T r = sol ? T(0) : T(rho[s * N + i]);
+#pragma unroll
     for (int qd = 0; qd < 19; ++qd) {
-      const double cu = cx(qd) * uu[0] + cy(qd) * uu[1] + cz(qd) * uu[2];
-      const double feq = wq<double>(qd) * r * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
-      Store<S, T>::st(f, (size_t)(s * 19 + qd) * N + i, T(feq), wq<T>(qd) * k.shift[s]);
+      const T cu = T(cx(qd)) * uu[0] + T(cy(qd)) * uu[1] + T(cz(qd)) * uu[2];
+      const T feq = wq<T>(qd) * r * (T(1) + T(3) * cu + T(4.5) * cu * cu - T(1.5) * usq);
+      Store<S, T>::st(f, (size_t)(s * 19 + qd) * N + i, feq, wq<T>(qd) * k.shift[s]);
     }
   }
 }
@@ -552,15 +561,19 @@ __global__ void __launch_bounds__(256) k_obs(StepK<T> k, const S *__restrict__ f
     }
     if (k.solids) acc[4] += double(qc[i]);
     if (sol) continue;
-    double r[2] = {0.0, 0.0}, J[3] = {0.0, 0.0, 0.0};
+    T rt[2] = {T(0), T(0)}, Jt[3] = {T(0), T(0), T(0)};
+#pragma unroll
     for (int s = 0; s < NC; ++s)
+#pragma unroll
       for (int qd = 0; qd < 19; ++qd) {
-        const double v = double(Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]));
-        r[s] += v;
-        J[0] += cx(qd) * v;
-        J[1] += cy(qd) * v;
-        J[2] += cz(qd) * v;
+        const T v = Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]);
+        rt[s] += v;
+        if (cx(qd)) Jt[0] += T(cx(qd)) * v;
+        if (cy(qd)) Jt[1] += T(cy(qd)) * v;
+        if (cz(qd)) Jt[2] += T(cz(qd)) * v;
       }
+    const double r[2] = {double(rt[0]), double(rt[1])};
+    const double J[3] = {double(Jt[0]), double(Jt[1]), double(Jt[2])};
     acc[0] += r[0];
     acc[1] += r[1];
     acc[5] += J[0];
@@ -694,11 +707,13 @@ template <typename S, typename T> struct Launch {
     const S *f = (const S *)c.f[c.cur];
     const T *n = (const T *)c.n[c.ncur];
     if (c.ncomp == 2)
-      count_launch(), k_macro<S, T, 2><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, (T *)c.rho, (T *)c.psi, (T *)c.eps, (T *)c.q, n,
-                                                        (const T *)c.qc, (const T *)c.psi_s, c.solid);
+      count_launch(), k_macro<S, T, 2><<<grid_for(c.d.N, B), B, 0, c.s>>>(
+          k, f, (T *)c.rho, (T *)c.J, (T *)c.psi, (T *)c.eps, (T *)c.q, n, (const T *)c.qc, (const T *)c.psi_s,
+          c.solid);
     else
-      count_launch(), k_macro<S, T, 1><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, (T *)c.rho, (T *)c.psi, (T *)c.eps, (T *)c.q, n,
-                                                        (const T *)c.qc, (const T *)c.psi_s, c.solid);
+      count_launch(), k_macro<S, T, 1><<<grid_for(c.d.N, B), B, 0, c.s>>>(
+          k, f, (T *)c.rho, (T *)c.J, (T *)c.psi, (T *)c.eps, (T *)c.q, n, (const T *)c.qc, (const T *)c.psi_s,
+          c.solid);
   }
   static void virt(Ctx &c) {
     if (!c.solids || c.ncoll == 0) return;
@@ -713,8 +728,9 @@ template <typename S, typename T> struct Launch {
   template <int NC, bool SOL, bool IONS> static void collide_v(Ctx &c) {
     auto k = make_stepk<T>(c);
     count_launch(), k_collide<S, T, NC, SOL, IONS><<<grid_for(c.d.N, B), B, 0, c.s>>>(
-        k, (const S *)c.f[c.cur], (S *)c.f[1 - c.cur], (const T *)c.rho, (const T *)c.psi, (const T *)c.eps, c.phi,
-        (const T *)c.n[c.ncur], (const T *)c.psi_f, c.solid, c.owner, c.cv, (T *)c.u, (T *)c.flux);
+        k, (const S *)c.f[c.cur], (S *)c.f[1 - c.cur], (const T *)c.rho, (const T *)c.J, (const T *)c.psi,
+        (const T *)c.eps, (const T *)c.phit, (const T *)c.n[c.ncur], (const T *)c.psi_f, c.solid, c.owner, c.cv,
+        (T *)c.u, (T *)c.flux);
   }
   static void collide(Ctx &c) {
     const bool ions = c.nions > 0;

@@ -79,7 +79,7 @@ class lbeh_obs(C.Structure):
 
 class lbeh_profile(C.Structure):
     _fields_ = [("ms", C.c_double * LBEH_NSTAGES), ("calls", C.c_longlong * LBEH_NSTAGES),
-                ("launches", C.c_longlong)]
+                ("launches", C.c_longlong), ("poisson_cycles", C.c_longlong)]
 
 
 def _load():
@@ -316,7 +316,7 @@ class System:
         p = lbeh_profile_read(self.h)
         return {"ms": {STAGE_NAMES[k]: p.ms[k] for k in range(LBEH_NSTAGES)},
                 "calls": {STAGE_NAMES[k]: p.calls[k] for k in range(LBEH_NSTAGES)},
-                "launches": p.launches}
+                "launches": p.launches, "poisson_cycles": p.poisson_cycles}
 
     def get(self, what=("rho", "n", "phi", "u"), f=False):
         """Host FP64 copies of the requested fields."""

@@ -42,7 +42,7 @@ def test_struct_layouts_match_header(lib):
 #include <stddef.h>
 #include "lbeh.h"
 int main(void) {
-  printf("%zu %zu %zu\n", sizeof(lbeh_params), sizeof(lbeh_fields), sizeof(lbeh_obs));
+  printf("%zu %zu %zu %zu\n", sizeof(lbeh_params), sizeof(lbeh_fields), sizeof(lbeh_obs), sizeof(lbeh_profile));
   printf("%zu %zu %zu %zu\n", offsetof(lbeh_params, E_ext), offsetof(lbeh_params, stream),
          offsetof(lbeh_fields, ncolloid), offsetof(lbeh_obs, steps));
   return 0;
@@ -56,7 +56,8 @@ int main(void) {
         lines = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
     sizes = [int(v) for v in lines[0].split()]
     offs = [int(v) for v in lines[1].split()]
-    assert sizes == [C.sizeof(lib.lbeh_params), C.sizeof(lib.lbeh_fields), C.sizeof(lib.lbeh_obs)]
+    assert sizes == [C.sizeof(lib.lbeh_params), C.sizeof(lib.lbeh_fields), C.sizeof(lib.lbeh_obs),
+                     C.sizeof(lib.lbeh_profile)]
     assert offs == [lib.lbeh_params.E_ext.offset, lib.lbeh_params.stream.offset,
                     lib.lbeh_fields.ncolloid.offset, lib.lbeh_obs.steps.offset]
 
