@@ -209,6 +209,10 @@ int lbeh_observables_noalloc(int nx, int ny, int nz, int ncomp, int nions, int d
 /* Release all device state. */
 void lbeh_destroy(lbeh_handle *h);
 
+/* Text of the last CUDA failure seen by the handle (empty if none); owned by
+ * the handle, valid until its next call. */
+const char *lbeh_last_error(lbeh_handle *h);
+
 /* Static description of a status code. */
 const char *lbeh_status_string(int code);
 

@@ -44,8 +44,10 @@ struct Ctx {
   void *psi_s = nullptr;   // [N]
   void *psi_f = nullptr;   // [N]
   void *qc = nullptr;      // [N]
-  double *phi = nullptr;   // [N]
-  void *phit = nullptr;    // [N] potential in the compute type (aliases phi in FP64)
+  double *phi = nullptr;   // [N] FP64 potential (FP64 mode)
+  void *phit = nullptr;    // [N] potential in the compute type: aliases phi in FP64 mode; in the
+                           // FP32 modes the high words of the double-float potential phit + phi_lo
+  float *phi_lo = nullptr; // [N] low words of the double-float potential (FP32 modes)
   void *J = nullptr;       // [3][N] momentum sum_sigma sum_q f c_q
   uint8_t *solid = nullptr, *surface = nullptr;
   int *owner = nullptr;
@@ -106,6 +108,10 @@ int poisson_solve(Poisson *p, Ctx &c, double *relres);
 // conditional WHILE node driven by `handle`.  Returns 0 or -1.
 int poisson_capture(Poisson *p, Ctx &c, cudaGraphConditionalHandle handle);
 int poisson_read(Poisson *p, cudaStream_t s, PoissonStats *out);
+// false when the whole solve is one cooperative launch (no conditional node)
+bool poisson_needs_conditional(const Poisson *p);
+void phi_to_double(Ctx &c, double *out);       // FP64 values of the potential
+void phi_from_double(Ctx &c, const double *in);
 
 // Deterministic FP64 reductions (reduce.cu).
 void reduce_partials_final(const double *partials, int nblocks, int len, double *out, cudaStream_t s);

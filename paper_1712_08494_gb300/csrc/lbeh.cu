@@ -6,6 +6,7 @@
 // with bounce-back, Nernst-Planck update, colloid momentum exchange.
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -38,6 +39,7 @@ struct lbeh_handle {
   long long prof_calls[LBEH_NSTAGES] = {0};
   long long launches0 = 0;
   long long cycles0 = 0;
+  char last_error[256] = {0};  // text of the last CUDA failure
   // whole-step CUDA graphs, one per ping-pong parity
   cudaStream_t gs = nullptr;           // capture / replay stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -202,6 +204,14 @@ int check_params(const lbeh_params *p) {
   return LBEH_OK;
 }
 
+// Record the pending CUDA error (if any) in the handle and return LBEH_ERR_CUDA.
+int cuda_fail(lbeh_handle *h, const char *where) {
+  const cudaError_t e = cudaGetLastError();
+  snprintf(h->last_error, sizeof(h->last_error), "%s: %s", where,
+           e == cudaSuccess ? "failure reported by a CUDA call" : cudaGetErrorString(e));
+  return LBEH_ERR_CUDA;
+}
+
 void drop_graphs(lbeh_handle *h) {
   for (int k = 0; k < 2; ++k)
     if (h->exec[k]) {
@@ -222,11 +232,11 @@ int enqueue_step(lbeh_handle *h, Ctx &c, bool capture, cudaGraphConditionalHandl
   if (h->pois) {
     StageTimer st(h, LBEH_STAGE_POISSON);
     if (capture) {
-      if (poisson_capture(h->pois, c, handle) != 0) return LBEH_ERR_CUDA;
+      if (poisson_capture(h->pois, c, handle) != 0) return cuda_fail(h, "Poisson capture");
     } else {
       double rr = 0.0;
       const int it = poisson_solve(h->pois, c, &rr);
-      if (it == -1) return LBEH_ERR_CUDA;
+      if (it == -1) return cuda_fail(h, "Poisson solve");
       h->last_relres = rr;
       if (it < -1) {
         h->last_iters = -it - 2;
@@ -266,11 +276,11 @@ int build_graphs(lbeh_handle *h) {
     cc.ncur = cc.nions ? par : 0;
     const long long before = g_launches.load();
     if (cudaStreamBeginCapture(h->gs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-      rc = LBEH_ERR_CUDA;
+      rc = cuda_fail(h, "begin capture");
       break;
     }
     cudaGraphConditionalHandle handle = 0;
-    if (h->pois) {
+    if (h->pois && poisson_needs_conditional(h->pois)) {
       cudaStreamCaptureStatus cs;
       cudaGraph_t g = nullptr;
       if (cudaStreamGetCaptureInfo(h->gs, &cs, nullptr, &g, nullptr, nullptr, nullptr) != cudaSuccess ||
@@ -282,8 +292,9 @@ int build_graphs(lbeh_handle *h) {
     const cudaError_t e = cudaStreamEndCapture(h->gs, &graph);
     h->graph_launches = int(g_launches.load() - before);
     g_launches.fetch_sub(h->graph_launches);  // captured, not launched
-    if (rc == LBEH_OK && e != cudaSuccess) rc = LBEH_ERR_CUDA;
-    if (rc == LBEH_OK && cudaGraphInstantiate(&h->exec[par], graph, 0) != cudaSuccess) rc = LBEH_ERR_CUDA;
+    if (rc == LBEH_OK && e != cudaSuccess) rc = cuda_fail(h, "end capture");
+    if (rc == LBEH_OK && cudaGraphInstantiate(&h->exec[par], graph, 0) != cudaSuccess)
+      rc = cuda_fail(h, "graph instantiate");
     if (graph) cudaGraphDestroy(graph);
   }
   h->prof = prof;
@@ -364,11 +375,13 @@ int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
   ok &= (c.eps = dalloc(h, T * N)) != nullptr;
   ok &= (c.q = dalloc(h, T * N)) != nullptr;
   ok &= (c.u = dalloc(h, T * 3 * N)) != nullptr;
-  ok &= (c.phi = (double *)dalloc(h, 8 * N)) != nullptr;
-  if (p->prec == LBEH_FP64)
+  if (p->prec == LBEH_FP64) {
+    ok &= (c.phi = (double *)dalloc(h, 8 * N)) != nullptr;
     c.phit = c.phi;
-  else
+  } else {
     ok &= (c.phit = dalloc(h, 4 * N)) != nullptr;
+    ok &= (c.phi_lo = (float *)dalloc(h, 4 * N)) != nullptr;
+  }
   ok &= (c.J = dalloc(h, T * 3 * N)) != nullptr;
   ok &= (c.psi_s = dalloc(h, T * N)) != nullptr;
   ok &= (c.psi_f = dalloc(h, T * N)) != nullptr;
@@ -408,8 +421,11 @@ int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
     return LBEH_ERR_OOM;
   }
   cudaMemsetAsync(c.u, 0, T * 3 * N, c.s);
-  cudaMemsetAsync(c.phi, 0, 8 * N, c.s);
-  if (c.phit != c.phi) cudaMemsetAsync(c.phit, 0, 4 * N, c.s);
+  if (c.phi) cudaMemsetAsync(c.phi, 0, 8 * N, c.s);
+  if (c.phi_lo) {
+    cudaMemsetAsync(c.phit, 0, 4 * N, c.s);
+    cudaMemsetAsync(c.phi_lo, 0, 4 * N, c.s);
+  }
   cudaMemsetAsync(c.status, 0, sizeof(int), c.s);
   cudaMemsetAsync(c.cv, 0, 8 * 3 * nc, c.s);
   cudaMemsetAsync(c.cforce, 0, 8 * 3 * nc, c.s);
@@ -550,11 +566,13 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
   if (in->phi) {
     const double *pd = stage_in(h, in->phi, in->dtype, in->on_device, N, tmp);
     if (!pd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
-    cudaMemcpyAsync(c.phi, pd, 8 * N, cudaMemcpyDeviceToDevice, c.s);
-  } else {
+    phi_from_double(c, pd);
+  } else if (c.phi) {
     cudaMemsetAsync(c.phi, 0, 8 * N, c.s);
+  } else {
+    cudaMemsetAsync(c.phit, 0, 4 * N, c.s);
+    cudaMemsetAsync(c.phi_lo, 0, 4 * N, c.s);
   }
-  if (c.phit != c.phi) to_compute(h, c.phi, c.phit, N);
   cudaMemsetAsync(c.u, 0, (c.prec == LBEH_FP64 ? 8 : 4) * 3 * N, c.s);
   cudaMemsetAsync(c.status, 0, sizeof(int), c.s);
   if (h->pois && poisson_reset(h->pois, c.s) != 0) {
@@ -587,7 +605,7 @@ int lbeh_step(lbeh_handle *h, int nsteps) {
     cudaEventRecord(h->ev_in, c.s);
     cudaStreamWaitEvent(h->gs, h->ev_in, 0);
     for (int t = 0; t < nsteps; ++t) {
-      if (cudaGraphLaunch(h->exec[c.cur], h->gs) != cudaSuccess) return LBEH_ERR_CUDA;
+      if (cudaGraphLaunch(h->exec[c.cur], h->gs) != cudaSuccess) return cuda_fail(h, "graph launch");
       g_launches.fetch_add(h->graph_launches);
       c.cur ^= 1;
       if (c.nions) c.ncur ^= 1;
@@ -604,8 +622,8 @@ int lbeh_step(lbeh_handle *h, int nsteps) {
   }
   if (h->pois) {
     PoissonStats ps;
-    if (poisson_read(h->pois, graph ? h->gs : c.s, &ps) != 0) return LBEH_ERR_CUDA;
-    if (cudaStreamSynchronize(c.s) != cudaSuccess) return LBEH_ERR_CUDA;
+    if (poisson_read(h->pois, graph ? h->gs : c.s, &ps) != 0) return cuda_fail(h, "Poisson read-back");
+    if (cudaStreamSynchronize(c.s) != cudaSuccess) return cuda_fail(h, "step synchronise");
     if (graph) {
       g_launches.fetch_add((ps.total_iters - h->total_iters_seen) * ps.body_launches);
       h->last_iters = ps.iters;
@@ -616,9 +634,11 @@ int lbeh_step(lbeh_handle *h, int nsteps) {
     cudaMemcpy(&dst, c.status, sizeof(int), cudaMemcpyDeviceToHost);
     if (dst & ST_POISSON) h->status = LBEH_ERR_POISSON_NOT_CONVERGED;
   }
-  if (cudaGetLastError() != cudaSuccess) return LBEH_ERR_CUDA;
+  if (cudaPeekAtLastError() != cudaSuccess) return cuda_fail(h, "step");
   return h->status;
 }
+
+const char *lbeh_last_error(lbeh_handle *h) { return h ? h->last_error : "no handle"; }
 
 int lbeh_observables(lbeh_handle *h, lbeh_obs *out) {
   if (!h || !out) return LBEH_ERR_INVALID_ARG;
@@ -688,7 +708,13 @@ int lbeh_get_fields(lbeh_handle *h, lbeh_fields *out) {
     for (int s = 0; s < 2; ++s)
       if (out->n[s]) ok &= nd && stage_out(h, nd + s * N, out->n[s], out->dtype, out->on_device, N, tmp);
   }
-  if (out->phi) ok &= stage_out(h, c.phi, out->phi, out->dtype, out->on_device, N, tmp);
+  if (out->phi) {
+    double *pd = nullptr;
+    if (cudaMalloc(&pd, 8 * N) != cudaSuccess) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
+    tmp.push_back(pd);
+    phi_to_double(c, pd);
+    ok &= stage_out(h, pd, out->phi, out->dtype, out->on_device, N, tmp);
+  }
   const int nc = c.ncoll;
   if (nc && (out->cx || out->cv || out->cf)) {
     if (out->cx) cudaMemcpyAsync(out->cx, c.cx, 8 * 3 * nc, cudaMemcpyDeviceToHost, c.s);

@@ -20,6 +20,7 @@
 // CUDA graph the test drives a conditional WHILE node, so a whole timestep
 // runs without host round trips.
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 #include <utility>
 #include <vector>
@@ -49,21 +50,72 @@ template <typename T> struct Tail {
   Level<T> L[kMaxLevels];
 };
 
+// Double-float numbers (hi + lo, two FP32 words, ~48-bit significand) with
+// error-free transformations: the FP32 modes keep the potential and form the
+// defect-correction residual in this form, on the FP32 pipes (the FP64 rate
+// of the target is a small fraction of its FP32 rate).  Intrinsics keep the
+// compiler from contracting the compensated sums.
+struct DF {
+  float hi, lo;
+};
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return DF{s, e};
+}
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  DF s = two_sum(a.hi, b.hi);
+  const DF t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = fast_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return fast_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+__host__ __device__ inline DF df_split(double v) {
+  const float h = float(v);
+  return DF{h, float(v - double(h))};
+}
+
 // Device-side solver state.
 struct PDev {
   double mean_q, mean_phi, bnorm2, rnorm2, relres, tol;
+  DF mean_q_df, mean_phi_df;
   int iters, max_iter, cond, notconv;
   long long total_iters;
   int have_prev;  // phi_prev holds the solution of the previous step
   int zero;       // right-hand side vanishes: phi = 0
 };
 
+struct Bar;
 struct Poisson {
   int fp64 = 0;
   int nred = 0;               // blocks of the FP64 reduction passes (fixed per size)
+  int pgrid = 0;              // blocks of the persistent solve (0: not available)
+  size_t ptail_smem = 0;      // its dynamic shared memory
+  Bar *bar = nullptr;         // its grid barrier
   std::vector<Level<double>> Ld;
   std::vector<Level<float>> Lf;
   double *phi_prev = nullptr; // solution of the previous step (initial guess extrapolation)
+  float *prev_hi = nullptr, *prev_lo = nullptr;  // the same in double-float (FP32 modes)
   double *part = nullptr;     // reduction partials
   PDev *dev = nullptr;
   std::vector<void *> allocs;
@@ -260,9 +312,7 @@ template <typename T> __host__ __device__ inline size_t tail_bytes(const Tail<T>
 // V-cycle over levels first..n-1 of `tl` inside one block, with every level
 // held in shared memory: face coefficients and the right-hand side of level
 // `first` are loaded, the correction x of level `first` is written back.
-template <typename T> __global__ void __launch_bounds__(1024) k_tail(Tail<T> tl, int first) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ T sh[1024];
+template <typename T> __device__ void tail_vcycle(const Tail<T> &tl, int first, unsigned char *smem_raw, T *sh) {
   Tail<T> sl = tl;  // same levels, arrays redirected to shared memory
   {
     T *p = reinterpret_cast<T *>(smem_raw);
@@ -327,6 +377,12 @@ template <typename T> __global__ void __launch_bounds__(1024) k_tail(Tail<T> tl,
   for (long long i = threadIdx.x; i < tl.L[first].N; i += blockDim.x) tl.L[first].x[i] = sl.L[first].x[i];
 }
 
+template <typename T> __global__ void __launch_bounds__(1024) k_tail(Tail<T> tl, int first) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T sh[1024];
+  tail_vcycle(tl, first, smem_raw, sh);
+}
+
 // ---------------------------------------------------------------- FP64 driver kernels
 __device__ __forceinline__ double block_sum256(double v, double *sh) {
   sh[threadIdx.x] = v;
@@ -360,14 +416,18 @@ __global__ void __launch_bounds__(256) k_coef0_qsum(Dims d, const T *__restrict_
   if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
-// fixed-order sum of the partials, times scale, into *out
+// fixed-order sum of the partials, times scale, into *out (and its
+// double-float split into *out_df when given)
 __global__ void __launch_bounds__(256) k_sum_partials(const double *__restrict__ part, int nb,
-                                                      double *__restrict__ out, double scale) {
+                                                      double *__restrict__ out, double scale, DF *out_df) {
   __shared__ double sh[256];
   double acc = 0.0;
   for (int b = threadIdx.x; b < nb; b += 256) acc += part[b];
   const double r = block_sum256(acc, sh);
-  if (threadIdx.x == 0) *out = r * scale;
+  if (threadIdx.x == 0) {
+    *out = r * scale;
+    if (out_df) *out_df = df_split(r * scale);
+  }
 }
 
 // FP64 residual r = b - A phi with b = -(q - qbar) + sum_d k (E_ext.c_d)
@@ -436,6 +496,7 @@ __global__ void __launch_bounds__(256) k_check(const double *__restrict__ part, 
     }
     st->rnorm2 = r2;
     st->mean_phi = ps / double(n);
+    st->mean_phi_df = df_split(st->mean_phi);
     const double bn = st->bnorm2;
     const double rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
     st->relres = rr;
@@ -447,6 +508,103 @@ __global__ void __launch_bounds__(256) k_check(const double *__restrict__ part, 
     if (fail) atomicOr(status, ST_POISSON);
     if (use_handle) cudaGraphSetConditional(handle, more ? 1u : 0u);
   }
+}
+
+// ---------------------------------------------------------------- double-float driver kernels
+// residual r = b - A phi with phi = hi + lo and b = -(q - qbar) + sum_d k (E_ext.c_d)
+// in double-float; per-block partials [0] r^2, [1] b^2, [2] phi as in k_residual0
+__global__ void __launch_bounds__(256) k_residual_df(Level<float> L, const float *__restrict__ hi,
+                                                     const float *__restrict__ lo, const float *__restrict__ q,
+                                                     const PDev *__restrict__ st, DF ex, DF ey, DF ez,
+                                                     double *__restrict__ part, int nb) {
+  const Dims d = L.dims();
+  __shared__ double sh[256];
+  const DF qbar = st->mean_q_df;
+  float ar = 0.f, ab = 0.f, ap = 0.f;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < d.N; i += (long long)gridDim.x * 256) {
+    int x, y, z;
+    coords(d, i, x, y, z);
+    const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
+    const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
+    const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
+    const float kxp = L.k[0][i], kxm = L.k[0][ixm];
+    const float kyp = L.k[1][i], kym = L.k[1][iym];
+    const float kzp = L.k[2][i], kzm = L.k[2][izm];
+    const DF p{hi[i], lo[i]};
+    DF Ap = df_mul_f(df_sub(DF{hi[ixp], lo[ixp]}, p), kxp);
+    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[ixm], lo[ixm]}, p), kxm));
+    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[iyp], lo[iyp]}, p), kyp));
+    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[iym], lo[iym]}, p), kym));
+    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[izp], lo[izp]}, p), kzp));
+    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[izm], lo[izm]}, p), kzm));
+    DF b = df_sub(qbar, DF{q[i], 0.f});
+    if (ex.hi != 0.f) b = df_add(b, df_mul(ex, two_sum(kxp, -kxm)));
+    if (ey.hi != 0.f) b = df_add(b, df_mul(ey, two_sum(kyp, -kym)));
+    if (ez.hi != 0.f) b = df_add(b, df_mul(ez, two_sum(kzp, -kzm)));
+    const DF r = df_sub(b, Ap);
+    const float rf = __fadd_rn(r.hi, r.lo);
+    L.b[i] = rf;
+    ar = __fmaf_rn(rf, rf, ar);
+    ab = __fmaf_rn(b.hi, b.hi, ab);
+    ap = __fadd_rn(ap, p.hi);
+  }
+  double v = block_sum256(double(ar), sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = v;
+  v = block_sum256(double(ab), sh);
+  if (threadIdx.x == 0) part[nb + blockIdx.x] = v;
+  v = block_sum256(double(ap), sh);
+  if (threadIdx.x == 0) part[2 * nb + blockIdx.x] = v;
+}
+
+// phi += correction, in double-float
+__global__ void k_update_df(float *__restrict__ hi, float *__restrict__ lo, const float *__restrict__ x,
+                            long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const DF s = df_add(DF{hi[i], lo[i]}, DF{x[i], 0.f});
+  hi[i] = s.hi;
+  lo[i] = s.lo;
+}
+
+// initial guess 2 phi(t-1) - phi(t-2), in double-float
+__global__ void k_extrapolate_df(float *__restrict__ hi, float *__restrict__ lo, float *__restrict__ phi_hi,
+                                 float *__restrict__ phi_lo, long long n, const PDev *__restrict__ st) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const DF p{hi[i], lo[i]};
+  if (st->have_prev) {
+    const DF g = df_sub(DF{2.f * p.hi, 2.f * p.lo}, DF{phi_hi[i], phi_lo[i]});
+    hi[i] = g.hi;
+    lo[i] = g.lo;
+  }
+  phi_hi[i] = p.hi;
+  phi_lo[i] = p.lo;
+}
+
+// phi -= mean(phi), or phi = 0 for a vanishing right-hand side
+__global__ void k_center_df(float *__restrict__ hi, float *__restrict__ lo, long long n,
+                            const PDev *__restrict__ st) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  DF v{0.f, 0.f};
+  if (!st->zero) v = df_sub(DF{hi[i], lo[i]}, st->mean_phi_df);
+  hi[i] = v.hi;
+  lo[i] = v.lo;
+}
+
+__global__ void k_df_to_double(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ out,
+                               long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = double(hi[i]) + double(lo[i]);
+}
+
+__global__ void k_double_to_df(const double *__restrict__ in, float *__restrict__ hi, float *__restrict__ lo,
+                               long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const DF v = df_split(in[i]);
+  hi[i] = v.hi;
+  lo[i] = v.lo;
 }
 
 // initial guess phi(t) ~ 2 phi(t-1) - phi(t-2) once two solutions exist
@@ -477,6 +635,322 @@ template <typename T>
 __global__ void k_update_phi(double *__restrict__ phi, const T *__restrict__ x, long long n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) phi[i] += double(x[i]);
+}
+
+// ---------------------------------------------------------------- persistent solve
+// The whole solve in one cooperative launch: initial guess, coefficients, the
+// residual test and the defect-correction cycles, separated by grid-wide
+// barriers.  Every block evaluates the same fixed-order sums, so all blocks
+// take the same branches.  The barrier wait is bounded: a block that gives up
+// raises an abort flag and the device status, and every block then returns.
+constexpr int kPB = 512;
+constexpr long long kSpinLimit = 1LL << 24;  // polls of ~100 ns: about two seconds
+
+struct Bar {
+  unsigned count, gen;
+  int abort, pad;
+};
+
+template <typename T> struct PArgs {
+  Tail<T> lv;
+  int tail;                                    // first level relaxed by block 0 in shared memory
+  const T *eps, *q;
+  double *phi, *prev;                          // FP64 potential (FP64 mode)
+  float *phi_hi, *phi_lo, *prev_hi, *prev_lo;  // double-float potential (FP32 modes)
+  DF edf[3];
+  double ex, ey, ez;
+  PDev *st;
+  int *status;
+  double *part;  // [3][gridDim.x]
+  Bar *bar;
+};
+
+__device__ __forceinline__ bool grid_sync(Bar *bar, int *status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned *vgen = &bar->gen;
+    volatile int *vab = &bar->abort;
+    const unsigned g = *vgen;
+    __threadfence();
+    if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+      bar->count = 0;
+      __threadfence();
+      atomicAdd(&bar->gen, 1u);
+    } else {
+      long long spins = 0;
+      while (*vgen == g && !*vab) {
+        if (++spins > kSpinLimit) {
+          atomicExch(&bar->abort, 1);
+          atomicOr(status, ST_TIMEOUT);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+    ok = !*vab;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ double block_sum_n(double v, double *sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// fixed-order sum of nb partials, identical in every block
+__device__ __forceinline__ double sum_partials(const double *part, int nb, double *sh) {
+  double acc = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[b];
+  return block_sum_n(acc, sh);
+}
+
+template <typename T, bool DFM>
+__device__ __forceinline__ void residual_site(const PArgs<T> &a, const Level<T> &L0, long long i, double qbar,
+                                              DF qbar_df, double &ar, double &ab, double &ap) {
+  const Dims d = L0.dims();
+  int x, y, z;
+  coords(d, i, x, y, z);
+  const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
+  const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
+  const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
+  const T kxp = L0.k[0][i], kxm = L0.k[0][ixm];
+  const T kyp = L0.k[1][i], kym = L0.k[1][iym];
+  const T kzp = L0.k[2][i], kzm = L0.k[2][izm];
+  if constexpr (DFM) {
+    const float *hi = a.phi_hi, *lo = a.phi_lo;
+    const DF p{hi[i], lo[i]};
+    DF Ap = df_mul_f(df_sub(DF{hi[ixp], lo[ixp]}, p), kxp);
+    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[ixm], lo[ixm]}, p), kxm));
+    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[iyp], lo[iyp]}, p), kyp));
+    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[iym], lo[iym]}, p), kym));
+    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[izp], lo[izp]}, p), kzp));
+    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[izm], lo[izm]}, p), kzm));
+    DF b = df_sub(qbar_df, DF{float(a.q[i]), 0.f});
+    if (a.edf[0].hi != 0.f) b = df_add(b, df_mul(a.edf[0], two_sum(kxp, -kxm)));
+    if (a.edf[1].hi != 0.f) b = df_add(b, df_mul(a.edf[1], two_sum(kyp, -kym)));
+    if (a.edf[2].hi != 0.f) b = df_add(b, df_mul(a.edf[2], two_sum(kzp, -kzm)));
+    const DF r = df_sub(b, Ap);
+    const float rf = __fadd_rn(r.hi, r.lo);
+    L0.b[i] = T(rf);
+    ar += double(rf * rf);
+    ab += double(b.hi * b.hi);
+    ap += double(p.hi);
+  } else {
+    const double *phi = a.phi;
+    const double p = phi[i];
+    double b = -(double(a.q[i]) - qbar);
+    if (a.ex != 0.0) b += a.ex * (double(kxp) - double(kxm));
+    if (a.ey != 0.0) b += a.ey * (double(kyp) - double(kym));
+    if (a.ez != 0.0) b += a.ez * (double(kzp) - double(kzm));
+    const double Ap = double(kxp) * (phi[ixp] - p) - double(kxm) * (p - phi[ixm]) + double(kyp) * (phi[iyp] - p) -
+                      double(kym) * (p - phi[iym]) + double(kzp) * (phi[izp] - p) - double(kzm) * (p - phi[izm]);
+    const double r = b - Ap;
+    L0.b[i] = T(r);
+    ar += r * r;
+    ab += b * b;
+    ap += p;
+  }
+}
+
+// residual pass + fixed-order sums in every block; returns false on abort
+template <typename T, bool DFM>
+__device__ bool residual_pass(const PArgs<T> &a, const Level<T> &L0, double qbar, DF qbar_df, double *sh,
+                              double &r2, double &b2, double &ps) {
+  const long long G = (long long)gridDim.x * blockDim.x;
+  double ar = 0.0, ab = 0.0, ap = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L0.N; i += G)
+    residual_site<T, DFM>(a, L0, i, qbar, qbar_df, ar, ab, ap);
+  ar = block_sum_n(ar, sh);
+  ab = block_sum_n(ab, sh);
+  ap = block_sum_n(ap, sh);
+  const int nb = gridDim.x;
+  if (threadIdx.x == 0) {
+    a.part[blockIdx.x] = ar;
+    a.part[nb + blockIdx.x] = ab;
+    a.part[2 * nb + blockIdx.x] = ap;
+  }
+  if (!grid_sync(a.bar, a.status)) return false;
+  r2 = sum_partials(a.part, nb, sh);
+  b2 = sum_partials(a.part + nb, nb, sh);
+  ps = sum_partials(a.part + 2 * nb, nb, sh);
+  return true;
+}
+
+template <typename T, bool DFM>
+__global__ void __launch_bounds__(kPB) k_poisson(PArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ double sh[kPB];
+  __shared__ T sht[kPB];
+  const long long G = (long long)gridDim.x * blockDim.x;
+  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const Level<T> &L0 = a.lv.L[0];
+  const Dims d = L0.dims();
+  const long long N = d.N;
+  PDev *st = a.st;
+  const int have_prev = st->have_prev;
+
+  // initial guess, level-0 face coefficients, sum of q
+  double accq = 0.0;
+  for (long long i = gt; i < N; i += G) {
+    if constexpr (DFM) {
+      const DF p{a.phi_hi[i], a.phi_lo[i]};
+      if (have_prev) {
+        const DF g = df_sub(DF{2.f * p.hi, 2.f * p.lo}, DF{a.prev_hi[i], a.prev_lo[i]});
+        a.phi_hi[i] = g.hi;
+        a.phi_lo[i] = g.lo;
+      }
+      a.prev_hi[i] = p.hi;
+      a.prev_lo[i] = p.lo;
+    } else {
+      const double p = a.phi[i];
+      if (have_prev) a.phi[i] = 2.0 * p - a.prev[i];
+      a.prev[i] = p;
+    }
+    int x, y, z;
+    coords(d, i, x, y, z);
+    const T e = a.eps[i];
+    L0.k[0][i] = T(0.5) * (e + a.eps[site(d, wrapp(x, d.nx), y, z)]);
+    L0.k[1][i] = T(0.5) * (e + a.eps[site(d, x, wrapp(y, d.ny), z)]);
+    L0.k[2][i] = T(0.5) * (e + a.eps[site(d, x, y, wrapp(z, d.nz))]);
+    accq += double(a.q[i]);
+  }
+  accq = block_sum_n(accq, sh);
+  if (threadIdx.x == 0) a.part[blockIdx.x] = accq;
+  if (!grid_sync(a.bar, a.status)) return;
+  const double qbar = sum_partials(a.part, gridDim.x, sh) / double(N);
+  const DF qbar_df = df_split(qbar);
+  // coarse face coefficients, level by level
+  for (int l = 1; l < a.lv.n; ++l) {
+    const Level<T> &F = a.lv.L[l - 1], &C = a.lv.L[l];
+    const Dims f = F.dims(), c = C.dims();
+    for (long long I = gt; I < c.N; I += G) {
+      int X, Y, Z;
+      coords(c, I, X, Y, Z);
+      const int base[3] = {C.cf[0] ? 2 * X : X, C.cf[1] ? 2 * Y : Y, C.cf[2] ? 2 * Z : Z};
+      for (int ax = 0; ax < 3; ++ax) {
+        T acc = T(0);
+        int cnt = 0;
+        const int ra = C.cf[ax] ? 1 : 0;
+        const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
+        for (int t1 = 0; t1 <= C.cf[b1]; ++t1)
+          for (int t2 = 0; t2 <= C.cf[b2]; ++t2) {
+            int pp[3];
+            pp[ax] = base[ax] + ra;
+            pp[b1] = base[b1] + t1;
+            pp[b2] = base[b2] + t2;
+            acc += F.k[ax][site(f, pp[0], pp[1], pp[2])];
+            ++cnt;
+          }
+        C.k[ax][I] = acc / T(cnt);
+      }
+    }
+    if (!grid_sync(a.bar, a.status)) return;
+  }
+  // residual test
+  double r2, b2, ps;
+  if (!residual_pass<T, DFM>(a, L0, qbar, qbar_df, sh, r2, b2, ps)) return;
+  const double tol = st->tol;
+  const int max_iter = st->max_iter;
+  const double bn = b2;
+  double rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
+  int it = 0;
+  while (rr >= tol && it < max_iter) {
+    // V-cycle on the correction: levels above the tail, red-black smoothing
+    for (int l = 0; l < a.tail; ++l) {
+      const Level<T> &Ll = a.lv.L[l];
+      for (int s = 0; s < kNu; ++s) {
+        if (s == 0) {
+          // first red half sweep from x = 0 (neighbours are black and still unset)
+          const unsigned hx = unsigned(Ll.nx / 2);
+          for (long long t = gt; t < Ll.N / 2; t += G) {
+            const unsigned r = unsigned(t) / hx;
+            const int xh = int(unsigned(t) - r * hx);
+            const int z = int(r / unsigned(Ll.ny));
+            const int y = int(r - unsigned(z) * unsigned(Ll.ny));
+            const int x = 2 * xh + ((y + z) & 1);
+            const Dims dl = Ll.dims();
+            const long long i = site(dl, x, y, z);
+            const T diag = Ll.h[0] * (Ll.k[0][i] + Ll.k[0][site(dl, wrapm(x, dl.nx), y, z)]) +
+                           Ll.h[1] * (Ll.k[1][i] + Ll.k[1][site(dl, x, wrapm(y, dl.ny), z)]) +
+                           Ll.h[2] * (Ll.k[2][i] + Ll.k[2][site(dl, x, y, wrapm(z, dl.nz))]);
+            Ll.x[i] = -Ll.b[i] / diag;
+          }
+        } else {
+          rb_range(Ll, 0, gt, G);
+        }
+        if (!grid_sync(a.bar, a.status)) return;
+        rb_range(Ll, 1, gt, G);
+        if (!grid_sync(a.bar, a.status)) return;
+      }
+      restrict_range(Ll, a.lv.L[l + 1], gt, G);
+      if (!grid_sync(a.bar, a.status)) return;
+    }
+    if (blockIdx.x == 0) tail_vcycle(a.lv, a.tail, smem_raw, sht);
+    if (!grid_sync(a.bar, a.status)) return;
+    for (int l = a.tail - 1; l >= 0; --l) {
+      const Level<T> &Ll = a.lv.L[l];
+      prolong_range(Ll, a.lv.L[l + 1], gt, G);
+      if (!grid_sync(a.bar, a.status)) return;
+      for (int s = 0; s < kNu; ++s) {
+        rb_range(Ll, 0, gt, G);
+        if (!grid_sync(a.bar, a.status)) return;
+        rb_range(Ll, 1, gt, G);
+        if (!grid_sync(a.bar, a.status)) return;
+      }
+    }
+    // phi += correction
+    for (long long i = gt; i < N; i += G) {
+      if constexpr (DFM) {
+        const DF s = df_add(DF{a.phi_hi[i], a.phi_lo[i]}, DF{float(L0.x[i]), 0.f});
+        a.phi_hi[i] = s.hi;
+        a.phi_lo[i] = s.lo;
+      } else {
+        a.phi[i] += double(L0.x[i]);
+      }
+    }
+    if (!grid_sync(a.bar, a.status)) return;
+    if (!residual_pass<T, DFM>(a, L0, qbar, qbar_df, sh, r2, b2, ps)) return;
+    rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
+    ++it;
+  }
+  const bool zero = bn == 0.0;
+  const double mean_phi = ps / double(N);
+  const DF mean_df = df_split(mean_phi);
+  for (long long i = gt; i < N; i += G) {
+    if constexpr (DFM) {
+      DF v{0.f, 0.f};
+      if (!zero) v = df_sub(DF{a.phi_hi[i], a.phi_lo[i]}, mean_df);
+      a.phi_hi[i] = v.hi;
+      a.phi_lo[i] = v.lo;
+    } else {
+      a.phi[i] = zero ? 0.0 : a.phi[i] - mean_phi;
+    }
+  }
+  if (gt == 0) {
+    st->mean_q = qbar;
+    st->mean_phi = mean_phi;
+    st->bnorm2 = bn;
+    st->rnorm2 = r2;
+    st->relres = rr;
+    st->iters = it;
+    st->total_iters += it;
+    const int fail = rr >= tol;
+    st->notconv = fail;
+    st->cond = 0;
+    st->zero = zero;
+    st->have_prev = 1;
+    if (fail) atomicOr(a.status, ST_POISSON);
+  }
 }
 
 // ---------------------------------------------------------------- host
@@ -525,15 +999,93 @@ template <typename T> static bool setup(Poisson *p, const Dims &d) {
   return true;
 }
 
+template <typename T, bool DFM> static void persistent_setup(Poisson *p) {
+  auto &L = levels<T>(p);
+  const size_t ts = tail_start(L);
+  for (size_t l = 0; l < ts; ++l)
+    if (!L[l].rb) return;  // odd axes above the tail: multi-kernel path
+  Tail<T> tl;
+  tl.n = (int)L.size();
+  for (size_t l = 0; l < L.size(); ++l) tl.L[l] = L[l];
+  const size_t smem = tail_bytes(tl, (int)ts);
+  if (cudaFuncSetAttribute(k_poisson<T, DFM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return;
+  int dev = 0, nsm = 0, coop = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_poisson<T, DFM>, kPB, smem) != cudaSuccess ||
+      per < 1) {
+    cudaGetLastError();
+    return;
+  }
+  p->pgrid = nsm * std::min(per, 2);
+  p->ptail_smem = smem;
+}
+
+template <typename T, bool DFM> static int persistent_launch(Poisson *p, Ctx &c, cudaStream_t s) {
+  auto &L = levels<T>(p);
+  PArgs<T> a{};
+  a.lv.n = (int)L.size();
+  for (size_t l = 0; l < L.size(); ++l) a.lv.L[l] = L[l];
+  a.tail = (int)tail_start(L);
+  a.eps = (const T *)c.eps;
+  a.q = (const T *)c.q;
+  if constexpr (DFM) {
+    a.phi_hi = (float *)c.phit;
+    a.phi_lo = c.phi_lo;
+    a.prev_hi = p->prev_hi;
+    a.prev_lo = p->prev_lo;
+  } else {
+    a.phi = c.phi;
+    a.prev = p->phi_prev;
+  }
+  for (int k = 0; k < 3; ++k) a.edf[k] = df_split(c.Eext[k]);
+  a.ex = c.Eext[0];
+  a.ey = c.Eext[1];
+  a.ez = c.Eext[2];
+  a.st = p->dev;
+  a.status = c.status;
+  a.part = p->part;
+  a.bar = p->bar;
+  if (cudaMemsetAsync(&p->bar->abort, 0, sizeof(int), s) != cudaSuccess) return -1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p->pgrid);
+  cfg.blockDim = dim3(kPB);
+  cfg.dynamicSmemBytes = p->ptail_smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  count_launch();
+  return cudaLaunchKernelEx(&cfg, k_poisson<T, DFM>, a) == cudaSuccess ? 0 : -1;
+}
+
 Poisson *poisson_create(const Ctx &c, int fp64) {
   Poisson *p = new Poisson;
   p->fp64 = fp64;
   bool ok = fp64 ? setup<double>(p, c.d) : setup<float>(p, c.d);
-  p->phi_prev = alloc<double>(p, c.d.N);
+  if (fp64) {
+    p->phi_prev = alloc<double>(p, c.d.N);
+  } else {
+    p->prev_hi = alloc<float>(p, c.d.N);
+    p->prev_lo = alloc<float>(p, c.d.N);
+  }
   p->nred = int(std::min<long long>(std::max<long long>((c.d.N + 255) / 256, 1), 8192));
-  p->part = alloc<double>(p, 3 * p->nred + 8);
   p->dev = alloc<PDev>(p, 1);
-  if (!ok || !p->phi_prev || !p->part || !p->dev) {
+  p->bar = alloc<Bar>(p, 1);
+  if (p->bar) cudaMemset(p->bar, 0, sizeof(Bar));
+  // persistent solve: every level above the tail must be red-black colourable
+  if (p->bar) {
+    if (fp64)
+      persistent_setup<double, false>(p);
+    else
+      persistent_setup<float, true>(p);
+  }
+  p->part = alloc<double>(p, 3 * std::max(p->nred, p->pgrid) + 8);
+  if (!ok || (fp64 ? !p->phi_prev : (!p->prev_hi || !p->prev_lo)) || !p->part || !p->dev) {
     poisson_destroy(p);
     return nullptr;
   }
@@ -605,20 +1157,48 @@ static int enqueue(Poisson *p, Ctx &c, cudaGraphConditionalHandle handle, bool g
   const Dims d = c.d;
   const cudaStream_t s = c.s;
   Level<T> &l0 = L[0];
-  count_launch(), k_extrapolate<<<grid_for(d.N, B), B, 0, s>>>(c.phi, p->phi_prev, d.N, p->dev);
+  constexpr bool DFM = std::is_same<T, float>::value;  // double-float potential
+  if (p->pgrid > 0) {
+    // whole solve in one cooperative launch
+    if (persistent_launch<T, DFM>(p, c, s) != 0) return -1;
+    p->body_launches = 0;
+    if (graph) return 0;
+    PDev hd{};
+    if (cudaMemcpyAsync(&hd, p->dev, sizeof(PDev), cudaMemcpyDeviceToHost, s) != cudaSuccess) return -1;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
+    *relres = hd.relres;
+    return hd.notconv ? -(hd.iters + 2) : hd.iters;
+  }
+  float *phi_hi = (float *)c.phit, *phi_lo = c.phi_lo;
+  const DF edf[3] = {df_split(c.Eext[0]), df_split(c.Eext[1]), df_split(c.Eext[2])};
+  auto residual = [&](cudaStream_t st) {
+    if constexpr (DFM)
+      count_launch(), k_residual_df<<<p->nred, 256, 0, st>>>(l0, phi_hi, phi_lo, (const float *)c.q, p->dev, edf[0],
+                                                             edf[1], edf[2], p->part, p->nred);
+    else
+      count_launch(), k_residual0<T><<<p->nred, 256, 0, st>>>(l0, c.phi, (const T *)c.q, p->dev, c.Eext[0],
+                                                              c.Eext[1], c.Eext[2], p->part, p->nred);
+  };
+  if constexpr (DFM)
+    count_launch(), k_extrapolate_df<<<grid_for(d.N, B), B, 0, s>>>(phi_hi, phi_lo, p->prev_hi, p->prev_lo, d.N,
+                                                                    p->dev);
+  else
+    count_launch(), k_extrapolate<<<grid_for(d.N, B), B, 0, s>>>(c.phi, p->phi_prev, d.N, p->dev);
   count_launch(), k_coef0_qsum<T><<<p->nred, 256, 0, s>>>(d, (const T *)c.eps, (const T *)c.q, l0.k[0], l0.k[1],
                                                          l0.k[2], p->part);
-  count_launch(), k_sum_partials<<<1, 256, 0, s>>>(p->part, p->nred, &p->dev->mean_q, 1.0 / double(d.N));
+  count_launch(), k_sum_partials<<<1, 256, 0, s>>>(p->part, p->nred, &p->dev->mean_q, 1.0 / double(d.N),
+                                                   &p->dev->mean_q_df);
   for (size_t li = 1; li < L.size(); ++li)
     count_launch(), k_coef_coarsen<T><<<grid_for(L[li].N, B), B, 0, s>>>(L[li - 1], L[li]);
-  count_launch(), k_residual0<T><<<p->nred, 256, 0, s>>>(l0, c.phi, (const T *)c.q, p->dev, c.Eext[0], c.Eext[1],
-                                                         c.Eext[2], p->part, p->nred);
+  residual(s);
   count_launch(), k_check<<<1, 256, 0, s>>>(p->part, p->nred, p->dev, c.status, 1, d.N, handle, graph ? 1 : 0);
   auto body = [&](cudaStream_t bs) {
     T *corr = vcycle(L, bs);
-    count_launch(), k_update_phi<T><<<grid_for(d.N, B), B, 0, bs>>>(c.phi, corr, d.N);
-    count_launch(), k_residual0<T><<<p->nred, 256, 0, bs>>>(l0, c.phi, (const T *)c.q, p->dev, c.Eext[0],
-                                                            c.Eext[1], c.Eext[2], p->part, p->nred);
+    if constexpr (DFM)
+      count_launch(), k_update_df<<<grid_for(d.N, B), B, 0, bs>>>(phi_hi, phi_lo, (const float *)corr, d.N);
+    else
+      count_launch(), k_update_phi<T><<<grid_for(d.N, B), B, 0, bs>>>(c.phi, corr, d.N);
+    residual(bs);
     count_launch(), k_check<<<1, 256, 0, bs>>>(p->part, p->nred, p->dev, c.status, 0, d.N, handle, graph ? 1 : 0);
   };
   PDev hd{};
@@ -663,9 +1243,11 @@ static int enqueue(Poisson *p, Ctx &c, cudaGraphConditionalHandle handle, bool g
       body(s);
     }
   }
-  // mean-free potential and its compute-type copy
-  count_launch(), k_center_copy<T><<<grid_for(d.N, 256), 256, 0, s>>>(
-      c.phi, d.N, p->dev, (void *)c.phit == (void *)c.phi ? nullptr : (T *)c.phit);
+  // mean-free potential (the hi words are the compute-type copy read by the step kernels)
+  if constexpr (DFM)
+    count_launch(), k_center_df<<<grid_for(d.N, 256), 256, 0, s>>>(phi_hi, phi_lo, d.N, p->dev);
+  else
+    count_launch(), k_center_copy<T><<<grid_for(d.N, 256), 256, 0, s>>>(c.phi, d.N, p->dev, (T *)nullptr);
   count_launch(), k_mark_prev<<<1, 1, 0, s>>>(p->dev);
   if (graph) return 0;
   *relres = hd.relres;
@@ -711,4 +1293,26 @@ int poisson_read(Poisson *p, cudaStream_t s, PoissonStats *out) {
   return 0;
 }
 
+}  // namespace lbeh
+
+namespace lbeh {
+// the potential as FP64 values (either representation)
+void phi_to_double(Ctx &c, double *out) {
+  if (c.prec == LBEH_FP64) {
+    cudaMemcpyAsync(out, c.phi, 8 * c.d.N, cudaMemcpyDeviceToDevice, c.s);
+  } else {
+    count_launch(), k_df_to_double<<<grid_for(c.d.N, 256), 256, 0, c.s>>>((const float *)c.phit, c.phi_lo, out, c.d.N);
+  }
+}
+void phi_from_double(Ctx &c, const double *in) {
+  if (c.prec == LBEH_FP64) {
+    cudaMemcpyAsync(c.phi, in, 8 * c.d.N, cudaMemcpyDeviceToDevice, c.s);
+  } else {
+    count_launch(), k_double_to_df<<<grid_for(c.d.N, 256), 256, 0, c.s>>>(in, (float *)c.phit, c.phi_lo, c.d.N);
+  }
+}
+}  // namespace lbeh
+
+namespace lbeh {
+bool poisson_needs_conditional(const Poisson *p) { return p->pgrid == 0; }
 }  // namespace lbeh

@@ -35,7 +35,7 @@ LBEH_AUX_QC, LBEH_AUX_EPS, LBEH_AUX_Q, LBEH_AUX_RHO_V, LBEH_AUX_U = 4, 5, 6, 7, 
 # exported symbols declared in include/lbeh.h
 SYMBOLS = ("lbeh_create", "lbeh_set_fields", "lbeh_get_fields", "lbeh_step", "lbeh_observables",
            "lbeh_get_aux", "lbeh_profile_enable", "lbeh_profile_read", "lbeh_observables_noalloc",
-           "lbeh_destroy", "lbeh_status_string")
+           "lbeh_last_error", "lbeh_destroy", "lbeh_status_string")
 LBEH_NOALLOC_MAX_SITES = 16777216
 
 LBEH_STAGE_MACRO, LBEH_STAGE_POISSON, LBEH_STAGE_COLLIDE, LBEH_STAGE_NP, LBEH_STAGE_COLLOID = 0, 1, 2, 3, 4
@@ -99,6 +99,8 @@ def _load():
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(lbeh_obs), C.c_void_p]
     lib.lbeh_destroy.argtypes = [H]
     lib.lbeh_destroy.restype = None
+    lib.lbeh_last_error.argtypes = [H]
+    lib.lbeh_last_error.restype = C.c_char_p
     lib.lbeh_status_string.argtypes = [C.c_int]
     lib.lbeh_status_string.restype = C.c_char_p
     for name in ("lbeh_create", "lbeh_set_fields", "lbeh_get_fields", "lbeh_step", "lbeh_observables",
@@ -141,12 +143,16 @@ def lbeh_get_fields(h, fields: lbeh_fields) -> int:
     return _check(_lib.lbeh_get_fields(h, C.byref(fields)), "lbeh_get_fields")
 
 
+def lbeh_last_error(h) -> str:
+    return _lib.lbeh_last_error(h).decode()
+
+
 def lbeh_step(h, nsteps: int) -> int:
     """Returns the status code; raises only on hard errors (not on a Poisson
     solve that missed its tolerance, which is reported by the status)."""
     rc = _lib.lbeh_step(h, int(nsteps))
     if rc not in (LBEH_OK, LBEH_ERR_POISSON_NOT_CONVERGED):
-        raise LbehError(rc, "lbeh_step")
+        raise LbehError(rc, "lbeh_step [%s]" % lbeh_last_error(h))
     return rc
 
 

@@ -183,3 +183,22 @@ def test_bitwise_reproducible(lbeh):
         sg.close()
     for k in outs[0]:
         assert np.array_equal(outs[0][k], outs[1][k]), k
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_fp32_modes_defect_correction_reaches_fp64_grade_residual(lbeh, prec):
+    """The FP32 modes keep the potential and the defect-correction residual in
+    double-float form, so the Poisson solve reaches relative residuals far
+    below the FP32 epsilon (here 1e-11) within the cycle cap, and the
+    potential agrees with the FP64 oracle to the FP32 rounding of its inputs."""
+    w = synth.droplet(n=24, r=7.0, prec=prec, tol=1e-11, Ez=0.02, charge=5.0, salt=2e-3)
+    w.params.poisson_max_iter = 60
+    so = oracle_for(w)
+    sg = gpu_for(w, lbeh)
+    step_both(sg, so, 2)
+    o = sg.observables()
+    assert o.status == lbeh.LBEH_OK
+    assert o.poisson_relres < 1e-11
+    errs = compare(sg, so, ("phi",))
+    assert errs["phi"] < 2e-4, errs
+    sg.close()
