@@ -360,7 +360,7 @@ template <typename T> __device__ void tail_vcycle(const Tail<T> &tl, int first, 
         L.x[i] = T(0);
       }
       __syncthreads();
-      tail_smooth(L, L.rb ? 16 : 48);
+      tail_smooth(L, L.rb ? 10 : 30);
     } else {
       for (long long i = threadIdx.x; i < L.N; i += blockDim.x) L.x[i] = T(0);
       __syncthreads();
@@ -644,7 +644,9 @@ __global__ void k_update_phi(double *__restrict__ phi, const T *__restrict__ x, 
 // take the same branches.  The barrier wait is bounded: a block that gives up
 // raises an abort flag and the device status, and every block then returns.
 constexpr int kPB = 512;
-constexpr long long kSpinLimit = 1LL << 24;  // polls of ~100 ns: about two seconds
+constexpr long long kSpinLimit = 1LL << 24;
+constexpr double kTrustTol = 1e-8;  // FP32 residual estimate used only above this tolerance
+constexpr double kEstErr = 1e-4;    // bound of its error relative to the last exact residual  // polls of ~100 ns: about two seconds
 
 struct Bar {
   unsigned count, gen;
@@ -787,7 +789,7 @@ __device__ bool residual_pass(const PArgs<T> &a, const Level<T> &L0, double qbar
 }
 
 template <typename T, bool DFM>
-__global__ void __launch_bounds__(kPB) k_poisson(PArgs<T> a) {
+__global__ void __launch_bounds__(kPB, 2) k_poisson(PArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[kPB];
   __shared__ T sht[kPB];
@@ -864,7 +866,16 @@ __global__ void __launch_bounds__(kPB) k_poisson(PArgs<T> a) {
   const double bn = b2;
   double rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
   int it = 0;
+  // In the FP32 modes the level-0 residual is carried from cycle to cycle in
+  // FP32 (r <- r - A e); that estimate is accurate to about 1e-5 of the
+  // starting residual, so below kTrustTol the exact double-float residual
+  // re-anchors it before convergence is accepted.
+  bool exact = true;
+  const bool carry = DFM && tol >= kTrustTol;
+  double rr0 = rr;
+  for (;;) {
   while (rr >= tol && it < max_iter) {
+    exact = !carry;
     // V-cycle on the correction: levels above the tail, red-black smoothing
     for (int l = 0; l < a.tail; ++l) {
       const Level<T> &Ll = a.lv.L[l];
@@ -908,20 +919,62 @@ __global__ void __launch_bounds__(kPB) k_poisson(PArgs<T> a) {
         if (!grid_sync(a.bar, a.status)) return;
       }
     }
-    // phi += correction
-    for (long long i = gt; i < N; i += G) {
-      if constexpr (DFM) {
-        const DF s = df_add(DF{a.phi_hi[i], a.phi_lo[i]}, DF{float(L0.x[i]), 0.f});
+    // phi += correction; the residual follows the correction
+    if (carry) {
+      // FP32 modes: r <- r - A e on the FP32 level-0 residual (its rounding error is
+      // relative to |A e| ~ |r|), phi += e in double-float; the double-float residual
+      // of the first pass fixes the starting point of each solve
+      double ar = 0.0, ap = 0.0;
+      for (long long i = gt; i < N; i += G) {
+        int x, y, z;
+        coords(d, i, x, y, z);
+        const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
+        const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
+        const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
+        const T* e = L0.x;
+        const T ei = e[i];
+        const T Ae = L0.k[0][i] * (e[ixp] - ei) + L0.k[0][ixm] * (e[ixm] - ei) + L0.k[1][i] * (e[iyp] - ei) +
+                     L0.k[1][iym] * (e[iym] - ei) + L0.k[2][i] * (e[izp] - ei) + L0.k[2][izm] * (e[izm] - ei);
+        const T r = L0.b[i] - Ae;
+        L0.b[i] = r;
+        ar += double(r * r);
+        const DF s = df_add(DF{a.phi_hi[i], a.phi_lo[i]}, DF{float(ei), 0.f});
         a.phi_hi[i] = s.hi;
         a.phi_lo[i] = s.lo;
-      } else {
-        a.phi[i] += double(L0.x[i]);
+        ap += double(s.hi);
       }
+      ar = block_sum_n(ar, sh);
+      ap = block_sum_n(ap, sh);
+      const int nb = gridDim.x;
+      if (threadIdx.x == 0) {
+        a.part[blockIdx.x] = ar;
+        a.part[2 * nb + blockIdx.x] = ap;
+      }
+      if (!grid_sync(a.bar, a.status)) return;
+      r2 = sum_partials(a.part, nb, sh);
+      ps = sum_partials(a.part + 2 * nb, nb, sh);
+    } else {
+      for (long long i = gt; i < N; i += G) {
+        if constexpr (DFM) {
+          const DF s = df_add(DF{a.phi_hi[i], a.phi_lo[i]}, DF{float(L0.x[i]), 0.f});
+          a.phi_hi[i] = s.hi;
+          a.phi_lo[i] = s.lo;
+        } else {
+          a.phi[i] += double(L0.x[i]);
+        }
+      }
+      if (!grid_sync(a.bar, a.status)) return;
+      if (!residual_pass<T, DFM>(a, L0, qbar, qbar_df, sh, r2, b2, ps)) return;
     }
-    if (!grid_sync(a.bar, a.status)) return;
-    if (!residual_pass<T, DFM>(a, L0, qbar, qbar_df, sh, r2, b2, ps)) return;
     rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
     ++it;
+  }
+  if (exact || rr + kEstErr * rr0 < tol) break;
+  if (!residual_pass<T, DFM>(a, L0, qbar, qbar_df, sh, r2, b2, ps)) return;
+  rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
+  rr0 = rr;
+  exact = true;
+  if (rr < tol || it >= max_iter) break;
   }
   const bool zero = bn == 0.0;
   const double mean_phi = ps / double(N);
