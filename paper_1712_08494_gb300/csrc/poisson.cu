@@ -649,9 +649,53 @@ constexpr double kTrustTol = 1e-8;  // FP32 residual estimate used only above th
 constexpr double kEstErr = 1e-4;    // bound of its error relative to the last exact residual  // polls of ~100 ns: about two seconds
 
 struct Bar {
-  unsigned count, gen;
+  unsigned long long arrived;  // monotonic arrival count (reset before each launch)
   int abort, pad;
 };
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long *p, unsigned long long v) {
+  unsigned long long o;
+  asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(o) : "l"(p), "l"(v) : "memory");
+  return o;
+}
+__device__ __forceinline__ int ld_acquire_s32(const int *p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid barrier: thread 0 of every block arrives with an acquire-release add
+// on a monotonic counter (releasing the block's writes, ordered by the
+// preceding __syncthreads) and polls it with acquire loads until all blocks of
+// this round have arrived.  The wait is bounded; on time-out the block raises
+// the abort flag and the status, and every block leaves at its next barrier.
+__device__ __forceinline__ bool grid_sync(Bar *bar, int *status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long nb = gridDim.x;
+    const unsigned long long old = atom_add_acq_rel_u64(&bar->arrived, 1ull);
+    const unsigned long long target = (old / nb + 1) * nb;
+    long long spins = 0;
+    while (ld_acquire_u64(&bar->arrived) < target) {
+      if (ld_acquire_s32(&bar->abort)) break;
+      if (++spins > kSpinLimit) {
+        atomicExch(&bar->abort, 1);
+        atomicOr(status, ST_TIMEOUT);
+        break;
+      }
+      __nanosleep(20);
+    }
+    ok = !ld_acquire_s32(&bar->abort);
+  }
+  __syncthreads();
+  return ok != 0;
+}
 
 template <typename T> struct PArgs {
   Tail<T> lv;
@@ -666,36 +710,6 @@ template <typename T> struct PArgs {
   double *part;  // [3][gridDim.x]
   Bar *bar;
 };
-
-__device__ __forceinline__ bool grid_sync(Bar *bar, int *status) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    volatile unsigned *vgen = &bar->gen;
-    volatile int *vab = &bar->abort;
-    const unsigned g = *vgen;
-    __threadfence();
-    if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
-      bar->count = 0;
-      __threadfence();
-      atomicAdd(&bar->gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g && !*vab) {
-        if (++spins > kSpinLimit) {
-          atomicExch(&bar->abort, 1);
-          atomicOr(status, ST_TIMEOUT);
-          break;
-        }
-        __nanosleep(100);
-      }
-    }
-    __threadfence();
-    ok = !*vab;
-  }
-  __syncthreads();
-  return ok != 0;
-}
 
 __device__ __forceinline__ double block_sum_n(double v, double *sh) {
   sh[threadIdx.x] = v;
@@ -1101,7 +1115,7 @@ template <typename T, bool DFM> static int persistent_launch(Poisson *p, Ctx &c,
   a.status = c.status;
   a.part = p->part;
   a.bar = p->bar;
-  if (cudaMemsetAsync(&p->bar->abort, 0, sizeof(int), s) != cudaSuccess) return -1;
+  if (cudaMemsetAsync(p->bar, 0, sizeof(Bar), s) != cudaSuccess) return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p->pgrid);
   cfg.blockDim = dim3(kPB);
