@@ -41,9 +41,37 @@ template <typename T> struct Level {
   T h[3] = {T(1), T(1), T(1)};  // 1 / H_a^2
   T *k[3] = {nullptr, nullptr, nullptr};
   T *x = nullptr, *x2 = nullptr, *b = nullptr;
+  const T *eps = nullptr;  // set: face coefficients (eps_i + eps_{i+a})/2 formed from eps, k unused
   bool rb = false;
   __host__ __device__ Dims dims() const { return Dims{nx, ny, nz, N}; }
 };
+
+// face coefficients k_a(i) (p: +a face) and k_a(i-a) (m) of a cell
+template <typename T> struct Faces {
+  T xp, xm, yp, ym, zp, zm;
+};
+template <typename T>
+__device__ __forceinline__ Faces<T> faces(const Level<T> &L, long long i, long long ixp, long long ixm, long long iyp,
+                                          long long iym, long long izp, long long izm) {
+  Faces<T> f;
+  if (L.eps) {
+    const T e = L.eps[i];
+    f.xp = T(0.5) * (e + L.eps[ixp]);
+    f.xm = T(0.5) * (L.eps[ixm] + e);
+    f.yp = T(0.5) * (e + L.eps[iyp]);
+    f.ym = T(0.5) * (L.eps[iym] + e);
+    f.zp = T(0.5) * (e + L.eps[izp]);
+    f.zm = T(0.5) * (L.eps[izm] + e);
+  } else {
+    f.xp = L.k[0][i];
+    f.xm = L.k[0][ixm];
+    f.yp = L.k[1][i];
+    f.ym = L.k[1][iym];
+    f.zp = L.k[2][i];
+    f.zm = L.k[2][izm];
+  }
+  return f;
+}
 
 template <typename T> struct Tail {
   int n = 0;
@@ -112,6 +140,7 @@ struct Poisson {
   int pgrid = 0;              // blocks of the persistent solve (0: not available)
   size_t ptail_smem = 0;      // its dynamic shared memory
   Bar *bar = nullptr;         // its grid barrier
+  void *dlevels = nullptr;    // its level table (device)
   std::vector<Level<double>> Ld;
   std::vector<Level<float>> Lf;
   double *phi_prev = nullptr; // solution of the previous step (initial guess extrapolation)
@@ -129,9 +158,8 @@ __device__ __forceinline__ void stencil(const Dims &d, const Level<T> &L, long l
   const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
   const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
   const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
-  const T kxp = L.k[0][i], kxm = L.k[0][ixm];
-  const T kyp = L.k[1][i], kym = L.k[1][iym];
-  const T kzp = L.k[2][i], kzm = L.k[2][izm];
+  const Faces<T> f = faces(L, i, ixp, ixm, iyp, iym, izp, izm);
+  const T kxp = f.xp, kxm = f.xm, kyp = f.yp, kym = f.ym, kzp = f.zp, kzm = f.zm;
   off = L.h[0] * (kxp * xv[ixp] + kxm * xv[ixm]) + L.h[1] * (kyp * xv[iyp] + kym * xv[iym]) +
         L.h[2] * (kzp * xv[izp] + kzm * xv[izm]);
   diag = L.h[0] * (kxp + kxm) + L.h[1] * (kyp + kym) + L.h[2] * (kzp + kzm);
@@ -312,38 +340,56 @@ template <typename T> __host__ __device__ inline size_t tail_bytes(const Tail<T>
 // V-cycle over levels first..n-1 of `tl` inside one block, with every level
 // held in shared memory: face coefficients and the right-hand side of level
 // `first` are loaded, the correction x of level `first` is written back.
-template <typename T> __device__ void tail_vcycle(const Tail<T> &tl, int first, unsigned char *smem_raw, T *sh) {
-  Tail<T> sl = tl;  // same levels, arrays redirected to shared memory
-  {
+// V-cycle over levels first..n-1 of lv inside one block, every level held in
+// shared memory (descriptors included): face coefficients and the right-hand
+// side of level `first` are loaded, its correction x is written back.
+template <typename T>
+__device__ void tail_vcycle(const Level<T> *__restrict__ lv, int n, int first, unsigned char *smem_raw, T *sh) {
+  __shared__ Level<T> sl[kMaxLevels];
+  if (threadIdx.x == 0) {
     T *p = reinterpret_cast<T *>(smem_raw);
-    for (int l = first; l < tl.n; ++l) {
-      Level<T> &L = sl.L[l];
-      const long long n = L.N;
+    for (int l = first; l < n; ++l) {
+      Level<T> L = lv[l];
+      const long long m = L.N;
       for (int a = 0; a < 3; ++a) {
         L.k[a] = p;
-        p += n;
+        p += m;
       }
       L.x = p;
-      p += n;
+      p += m;
       L.b = p;
-      p += n;
+      p += m;
       if (!L.rb) {
         L.x2 = p;
-        p += n;
+        p += m;
       }
-    }
-  }
-  for (int l = first; l < tl.n; ++l) {
-    const long long n = tl.L[l].N;
-    for (long long i = threadIdx.x; i < n; i += blockDim.x) {
-      for (int a = 0; a < 3; ++a) sl.L[l].k[a][i] = tl.L[l].k[a][i];
-      if (l == first) sl.L[l].b[i] = tl.L[l].b[i];
+      L.eps = nullptr;
+      sl[l] = L;
     }
   }
   __syncthreads();
-  for (int l = first; l < sl.n; ++l) {
-    const Level<T> &L = sl.L[l];
-    if (l == sl.n - 1) {
+  for (int l = first; l < n; ++l) {
+    const Level<T> G = lv[l];
+    const Level<T> S = sl[l];
+    const Dims dg = G.dims();
+    for (long long i = threadIdx.x; i < G.N; i += blockDim.x) {
+      if (G.eps) {
+        int x, y, z;
+        coords(dg, i, x, y, z);
+        const T e = G.eps[i];
+        S.k[0][i] = T(0.5) * (e + G.eps[site(dg, wrapp(x, dg.nx), y, z)]);
+        S.k[1][i] = T(0.5) * (e + G.eps[site(dg, x, wrapp(y, dg.ny), z)]);
+        S.k[2][i] = T(0.5) * (e + G.eps[site(dg, x, y, wrapp(z, dg.nz))]);
+      } else {
+        for (int a = 0; a < 3; ++a) S.k[a][i] = G.k[a][i];
+      }
+      if (l == first) S.b[i] = G.b[i];
+    }
+  }
+  __syncthreads();
+  for (int l = first; l < n; ++l) {
+    const Level<T> L = sl[l];
+    if (l == n - 1) {
       // coarsest: mean-free right-hand side, fixed relaxation count
       T acc = T(0);
       for (long long i = threadIdx.x; i < L.N; i += blockDim.x) acc += L.b[i];
@@ -365,22 +411,27 @@ template <typename T> __device__ void tail_vcycle(const Tail<T> &tl, int first, 
       for (long long i = threadIdx.x; i < L.N; i += blockDim.x) L.x[i] = T(0);
       __syncthreads();
       tail_smooth(L, kNu);
-      restrict_range(L, sl.L[l + 1], threadIdx.x, blockDim.x);
+      const Level<T> Lc = sl[l + 1];
+      restrict_range(L, Lc, threadIdx.x, blockDim.x);
       __syncthreads();
     }
   }
-  for (int l = sl.n - 2; l >= first; --l) {
-    prolong_range(sl.L[l], sl.L[l + 1], threadIdx.x, blockDim.x);
+  for (int l = n - 2; l >= first; --l) {
+    const Level<T> Lf = sl[l], Lc = sl[l + 1];
+    prolong_range(Lf, Lc, threadIdx.x, blockDim.x);
     __syncthreads();
-    tail_smooth(sl.L[l], kNu);
+    tail_smooth(Lf, kNu);
   }
-  for (long long i = threadIdx.x; i < tl.L[first].N; i += blockDim.x) tl.L[first].x[i] = sl.L[first].x[i];
+  {
+    const Level<T> G = lv[first], S = sl[first];
+    for (long long i = threadIdx.x; i < G.N; i += blockDim.x) G.x[i] = S.x[i];
+  }
 }
 
 template <typename T> __global__ void __launch_bounds__(1024) k_tail(Tail<T> tl, int first) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T sh[1024];
-  tail_vcycle(tl, first, smem_raw, sh);
+  tail_vcycle(tl.L, tl.n, first, smem_raw, sh);
 }
 
 // ---------------------------------------------------------------- FP64 driver kernels
@@ -698,7 +749,8 @@ __device__ __forceinline__ bool grid_sync(Bar *bar, int *status) {
 }
 
 template <typename T> struct PArgs {
-  Tail<T> lv;
+  const Level<T> *lv;                          // level table in device memory
+  int nlev;
   int tail;                                    // first level relaxed by block 0 in shared memory
   const T *eps, *q;
   double *phi, *prev;                          // FP64 potential (FP64 mode)
@@ -739,9 +791,8 @@ __device__ __forceinline__ void residual_site(const PArgs<T> &a, const Level<T> 
   const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
   const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
   const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
-  const T kxp = L0.k[0][i], kxm = L0.k[0][ixm];
-  const T kyp = L0.k[1][i], kym = L0.k[1][iym];
-  const T kzp = L0.k[2][i], kzm = L0.k[2][izm];
+  const Faces<T> fc = faces(L0, i, ixp, ixm, iyp, iym, izp, izm);
+  const T kxp = fc.xp, kxm = fc.xm, kyp = fc.yp, kym = fc.ym, kzp = fc.zp, kzm = fc.zm;
   if constexpr (DFM) {
     const float *hi = a.phi_hi, *lo = a.phi_lo;
     const DF p{hi[i], lo[i]};
@@ -809,7 +860,7 @@ __global__ void __launch_bounds__(kPB, 2) k_poisson(PArgs<T> a) {
   __shared__ T sht[kPB];
   const long long G = (long long)gridDim.x * blockDim.x;
   const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const Level<T> &L0 = a.lv.L[0];
+  const Level<T> L0 = a.lv[0];  // descriptors by value: stores cannot alias them
   const Dims d = L0.dims();
   const long long N = d.N;
   PDev *st = a.st;
@@ -832,12 +883,14 @@ __global__ void __launch_bounds__(kPB, 2) k_poisson(PArgs<T> a) {
       if (have_prev) a.phi[i] = 2.0 * p - a.prev[i];
       a.prev[i] = p;
     }
-    int x, y, z;
-    coords(d, i, x, y, z);
-    const T e = a.eps[i];
-    L0.k[0][i] = T(0.5) * (e + a.eps[site(d, wrapp(x, d.nx), y, z)]);
-    L0.k[1][i] = T(0.5) * (e + a.eps[site(d, x, wrapp(y, d.ny), z)]);
-    L0.k[2][i] = T(0.5) * (e + a.eps[site(d, x, y, wrapp(z, d.nz))]);
+    if (!L0.eps) {
+      int x, y, z;
+      coords(d, i, x, y, z);
+      const T e = a.eps[i];
+      L0.k[0][i] = T(0.5) * (e + a.eps[site(d, wrapp(x, d.nx), y, z)]);
+      L0.k[1][i] = T(0.5) * (e + a.eps[site(d, x, wrapp(y, d.ny), z)]);
+      L0.k[2][i] = T(0.5) * (e + a.eps[site(d, x, y, wrapp(z, d.nz))]);
+    }
     accq += double(a.q[i]);
   }
   accq = block_sum_n(accq, sh);
@@ -846,8 +899,8 @@ __global__ void __launch_bounds__(kPB, 2) k_poisson(PArgs<T> a) {
   const double qbar = sum_partials(a.part, gridDim.x, sh) / double(N);
   const DF qbar_df = df_split(qbar);
   // coarse face coefficients, level by level
-  for (int l = 1; l < a.lv.n; ++l) {
-    const Level<T> &F = a.lv.L[l - 1], &C = a.lv.L[l];
+  for (int l = 1; l < a.nlev; ++l) {
+    const Level<T> F = a.lv[l - 1], C = a.lv[l];
     const Dims f = F.dims(), c = C.dims();
     for (long long I = gt; I < c.N; I += G) {
       int X, Y, Z;
@@ -864,7 +917,14 @@ __global__ void __launch_bounds__(kPB, 2) k_poisson(PArgs<T> a) {
             pp[ax] = base[ax] + ra;
             pp[b1] = base[b1] + t1;
             pp[b2] = base[b2] + t2;
-            acc += F.k[ax][site(f, pp[0], pp[1], pp[2])];
+            const long long fi = site(f, pp[0], pp[1], pp[2]);
+            if (F.eps) {
+              int q[3] = {pp[0], pp[1], pp[2]};
+              q[ax] = q[ax] + 1 == (ax == 0 ? f.nx : ax == 1 ? f.ny : f.nz) ? 0 : q[ax] + 1;
+              acc += T(0.5) * (F.eps[fi] + F.eps[site(f, q[0], q[1], q[2])]);
+            } else {
+              acc += F.k[ax][fi];
+            }
             ++cnt;
           }
         C.k[ax][I] = acc / T(cnt);
@@ -892,7 +952,8 @@ __global__ void __launch_bounds__(kPB, 2) k_poisson(PArgs<T> a) {
     exact = !carry;
     // V-cycle on the correction: levels above the tail, red-black smoothing
     for (int l = 0; l < a.tail; ++l) {
-      const Level<T> &Ll = a.lv.L[l];
+      const Level<T> Ll = a.lv[l];
+      const Level<T> Lc = a.lv[l + 1];
       for (int s = 0; s < kNu; ++s) {
         if (s == 0) {
           // first red half sweep from x = 0 (neighbours are black and still unset)
@@ -905,9 +966,10 @@ __global__ void __launch_bounds__(kPB, 2) k_poisson(PArgs<T> a) {
             const int x = 2 * xh + ((y + z) & 1);
             const Dims dl = Ll.dims();
             const long long i = site(dl, x, y, z);
-            const T diag = Ll.h[0] * (Ll.k[0][i] + Ll.k[0][site(dl, wrapm(x, dl.nx), y, z)]) +
-                           Ll.h[1] * (Ll.k[1][i] + Ll.k[1][site(dl, x, wrapm(y, dl.ny), z)]) +
-                           Ll.h[2] * (Ll.k[2][i] + Ll.k[2][site(dl, x, y, wrapm(z, dl.nz))]);
+            const Faces<T> fc = faces(Ll, i, site(dl, wrapp(x, dl.nx), y, z), site(dl, wrapm(x, dl.nx), y, z),
+                                      site(dl, x, wrapp(y, dl.ny), z), site(dl, x, wrapm(y, dl.ny), z),
+                                      site(dl, x, y, wrapp(z, dl.nz)), site(dl, x, y, wrapm(z, dl.nz)));
+            const T diag = Ll.h[0] * (fc.xp + fc.xm) + Ll.h[1] * (fc.yp + fc.ym) + Ll.h[2] * (fc.zp + fc.zm);
             Ll.x[i] = -Ll.b[i] / diag;
           }
         } else {
@@ -917,14 +979,15 @@ __global__ void __launch_bounds__(kPB, 2) k_poisson(PArgs<T> a) {
         rb_range(Ll, 1, gt, G);
         if (!grid_sync(a.bar, a.status)) return;
       }
-      restrict_range(Ll, a.lv.L[l + 1], gt, G);
+      restrict_range(Ll, Lc, gt, G);
       if (!grid_sync(a.bar, a.status)) return;
     }
-    if (blockIdx.x == 0) tail_vcycle(a.lv, a.tail, smem_raw, sht);
+    if (blockIdx.x == 0) tail_vcycle(a.lv, a.nlev, a.tail, smem_raw, sht);
     if (!grid_sync(a.bar, a.status)) return;
     for (int l = a.tail - 1; l >= 0; --l) {
-      const Level<T> &Ll = a.lv.L[l];
-      prolong_range(Ll, a.lv.L[l + 1], gt, G);
+      const Level<T> Ll = a.lv[l];
+      const Level<T> Lc = a.lv[l + 1];
+      prolong_range(Ll, Lc, gt, G);
       if (!grid_sync(a.bar, a.status)) return;
       for (int s = 0; s < kNu; ++s) {
         rb_range(Ll, 0, gt, G);
@@ -945,10 +1008,11 @@ __global__ void __launch_bounds__(kPB, 2) k_poisson(PArgs<T> a) {
         const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
         const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
         const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
-        const T* e = L0.x;
+        const T *e = L0.x;
         const T ei = e[i];
-        const T Ae = L0.k[0][i] * (e[ixp] - ei) + L0.k[0][ixm] * (e[ixm] - ei) + L0.k[1][i] * (e[iyp] - ei) +
-                     L0.k[1][iym] * (e[iym] - ei) + L0.k[2][i] * (e[izp] - ei) + L0.k[2][izm] * (e[izm] - ei);
+        const Faces<T> fc = faces(L0, i, ixp, ixm, iyp, iym, izp, izm);
+        const T Ae = fc.xp * (e[ixp] - ei) + fc.xm * (e[ixm] - ei) + fc.yp * (e[iyp] - ei) + fc.ym * (e[iym] - ei) +
+                     fc.zp * (e[izp] - ei) + fc.zm * (e[izm] - ei);
         const T r = L0.b[i] - Ae;
         L0.b[i] = r;
         ar += double(r * r);
@@ -1066,7 +1130,7 @@ template <typename T> static bool setup(Poisson *p, const Dims &d) {
   return true;
 }
 
-template <typename T, bool DFM> static void persistent_setup(Poisson *p) {
+template <typename T, bool DFM> static void persistent_setup(Poisson *p, const Ctx &c) {
   auto &L = levels<T>(p);
   const size_t ts = tail_start(L);
   for (size_t l = 0; l < ts; ++l)
@@ -1086,6 +1150,12 @@ template <typename T, bool DFM> static void persistent_setup(Poisson *p) {
     cudaGetLastError();
     return;
   }
+  // level table in device memory; level 0 forms its face coefficients from eps
+  std::vector<Level<T>> tab(L.begin(), L.end());
+  if (ts > 0) tab[0].eps = (const T *)c.eps;
+  Level<T> *d = alloc<Level<T>>(p, (long long)tab.size());
+  if (!d || cudaMemcpy(d, tab.data(), tab.size() * sizeof(Level<T>), cudaMemcpyHostToDevice) != cudaSuccess) return;
+  p->dlevels = d;
   p->pgrid = nsm * std::min(per, 2);
   p->ptail_smem = smem;
 }
@@ -1093,8 +1163,8 @@ template <typename T, bool DFM> static void persistent_setup(Poisson *p) {
 template <typename T, bool DFM> static int persistent_launch(Poisson *p, Ctx &c, cudaStream_t s) {
   auto &L = levels<T>(p);
   PArgs<T> a{};
-  a.lv.n = (int)L.size();
-  for (size_t l = 0; l < L.size(); ++l) a.lv.L[l] = L[l];
+  a.lv = (const Level<T> *)p->dlevels;
+  a.nlev = (int)L.size();
   a.tail = (int)tail_start(L);
   a.eps = (const T *)c.eps;
   a.q = (const T *)c.q;
@@ -1147,9 +1217,9 @@ Poisson *poisson_create(const Ctx &c, int fp64) {
   // persistent solve: every level above the tail must be red-black colourable
   if (p->bar) {
     if (fp64)
-      persistent_setup<double, false>(p);
+      persistent_setup<double, false>(p, c);
     else
-      persistent_setup<float, true>(p);
+      persistent_setup<float, true>(p, c);
   }
   p->part = alloc<double>(p, 3 * std::max(p->nred, p->pgrid) + 8);
   if (!ok || (fp64 ? !p->phi_prev : (!p->prev_hi || !p->prev_lo)) || !p->part || !p->dev) {
