@@ -18,7 +18,9 @@ step: x(t+1) = x + v + F/(2m), v(t+1) = v + F/m, m = rho_p (4/3) pi r^3.
 Remap after the move (Sec. II.E, projection figure and the two node-conversion
 equations): a node covered by the colloid gives its fluid momentum to the
 colloid, its populations are removed and its ions are spread equally over its
-fluid D3Q19 neighbours; a node uncovered by the colloid is refilled with the
+D3Q19 neighbours that are fluid both before and after the move (reading: a
+neighbour uncovered in the same move starts with zero ions, so it receives
+none and ions are conserved exactly); a node uncovered by the colloid is refilled with the
 equilibrium at the mean density of its fluid neighbours and the colloid
 velocity, the colloid loses that momentum, and its ions start at zero.
 Reading: signs of the two momentum terms are those that conserve total
@@ -101,15 +103,16 @@ def move_and_remap(sys):
         for ax in range(3):
             np.add.at(dV[:, ax], own, mom[ax][created])
         if sys.nions:
+            kept = fluid_new & ~solid_old  # fluid before and after the move
             cnt = np.zeros(sys.shape)
             for q in range(1, Q):
-                cnt += shift(fluid_new, C[q])
+                cnt += shift(kept, C[q])
             share = np.where(created & (cnt > 0), 1.0 / np.maximum(cnt, 1.0), 0.0)
             add = np.zeros_like(sys.n)
             for q in range(1, Q):
                 # node y = x + c_q receives from created node x
                 for s in range(2):
-                    add[s] += shift(sys.n[s] * share, -C[q]) * fluid_new
+                    add[s] += shift(sys.n[s] * share, -C[q]) * kept
             sys.n = (sys.n + add) * fluid_new
         sys.f[:, :, created] = 0.0
 

@@ -445,3 +445,57 @@ def test_coupled_step_conserves_mass_ions_charge_with_fixed_colloid():
     assert np.allclose(c1["ions"], c0["ions"], rtol=1e-14)
     assert abs(c1["charge"]) < 1e-12
     assert s.poisson_relres < w.params.poisson_tol
+
+
+# ---------------------------------------------------------------- moving colloids
+def _moving_system(n=16, V=(0.03, -0.02, 0.01), nions=0, Q=0.0, E=(0.0, 0.0, 0.0), X=(7.45, 8.2, 7.9)):
+    p = synth.Params(nx=n, ny=n, nz=n, ncomp=1, nions=nions, prec="fp64", G=0.0, ncolloid_max=1,
+                     colloids_move=1, poisson_tol=1e-12, poisson_max_iter=500, E_ext=E, eps_r=(1.0, 1.0))
+    kw = {"n": np.full((2, n, n, n), 0.01)} if nions else {}
+    return OracleSystem(p, np.ones((1, n, n, n)), colloid_x=[list(X)], colloid_v=[list(V)],
+                        colloid_q=[Q], colloid_r=[3.0], **kw)
+
+
+def _total_momentum(s):
+    c = obs.conserved(s)
+    return np.array(c["momentum"]) + (s.cmass[:, None] * s.cv).sum(axis=0)
+
+
+def test_moving_colloid_conserves_total_momentum_across_remaps():
+    """Bounce-back exchange, node covering (fluid momentum to the colloid) and
+    uncovering (refill momentum from the colloid) with velocity-Verlet keep
+    fluid + colloid momentum constant to round-off (Sec. II.E); the colloid
+    crosses lattice nodes during the run so both conversions occur."""
+    s = _moving_system(V=(0.2, -0.15, 0.1))
+    p0 = _total_momentum(s)
+    solid0 = s.solid.copy()
+    for _ in range(6):
+        s.step()
+    assert not np.array_equal(solid0, s.solid)   # nodes were created and deleted
+    assert np.allclose(_total_momentum(s), p0, rtol=0, atol=1e-12)
+
+
+def test_moving_colloid_remap_conserves_ions():
+    s = _moving_system(V=(0.2, 0.1, -0.1), nions=2)
+    n0 = s.n.sum(axis=(1, 2, 3))
+    for _ in range(6):
+        s.step()
+    assert np.allclose(s.n.sum(axis=(1, 2, 3)), n0, rtol=1e-13)
+    assert (s.n[:, s.solid] == 0).all()
+
+
+def test_moving_colloid_is_dragged_by_the_fluid():
+    s = _moving_system(V=(0.02, 0.0, 0.0))
+    v0 = s.cv[0, 0]
+    s.run(10)
+    assert 0.0 < s.cv[0, 0] < v0          # decelerates, does not reverse
+    assert abs(s.cv[0, 1]) < 1e-3 * v0
+
+
+def test_negative_colloid_drifts_against_the_field():
+    """Electric force sum q_c E on the surface nodes (Sec. II.E): a negatively
+    charged colloid at rest in salt accelerates against the applied field."""
+    s = _moving_system(V=(0.0, 0.0, 0.0), nions=2, Q=-5.0, E=(1e-3, 0.0, 0.0))
+    s.n[0][s.fluid] += 5.0 / s.fluid.sum()   # neutralise with counter-cations
+    s.run(3)
+    assert s.cv[0, 0] < 0.0
