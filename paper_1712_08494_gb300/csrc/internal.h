@@ -51,10 +51,15 @@ struct Ctx {
   void *J = nullptr;       // [3][N] momentum sum_sigma sum_q f c_q
   uint8_t *solid = nullptr, *surface = nullptr;
   int *owner = nullptr;
+  uint8_t *solid_old = nullptr;  // geometry before the colloid move (moving colloids)
+  int *owner_old = nullptr;
 
   int ncoll = 0, ncoll_max = 0;
   double *cx = nullptr, *cv = nullptr, *cq = nullptr, *cr = nullptr;  // device colloid table
-  double *cforce = nullptr;  // [ncoll][3]
+  double *cforce = nullptr;  // [ncoll][3] total force of the step
+  double *cdp = nullptr;     // [ncoll][3] momentum change of the remap
+  bool moving = false;
+  double rho_p = 5.0, k_hertz = 1.0;
   int *ccount = nullptr;     // [ncoll] surface node counts
   int *status = nullptr;     // device status word
 
@@ -75,7 +80,8 @@ struct PrecOps {
   void (*collide)(Ctx &);
   void (*np)(Ctx &);
   void (*obs_partials)(Ctx &, double *partials, int nblocks);  // kObsLen doubles per block
-  void (*colloid_bb)(Ctx &);                                    // momentum exchange into cforce
+  void (*colloid_bb)(Ctx &);                                    // momentum exchange + electric force into cforce
+  void (*remap)(Ctx &);                                         // node covering / uncovering after a move
 };
 PrecOps ops_f64();
 PrecOps ops_f32();
@@ -84,6 +90,11 @@ PrecOps ops_f16();
 
 constexpr int kObsLen = 16;  // see step_kernels.cuh obs layout
 constexpr int kRedBlocks = 512;
+
+// Colloid dynamics (colloids.cu): pair forces added to cforce, velocity-Verlet
+// when moving; velocity update by the remap momentum.
+void colloid_forces_move(Ctx &c);
+void colloid_apply_dp(Ctx &c);
 
 // Geometry (geometry.cu).
 void geometry_build(Ctx &c);  // solid, owner, psi_s, psi_f, surface, ccount, qc

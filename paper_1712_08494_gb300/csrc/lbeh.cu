@@ -257,8 +257,17 @@ int enqueue_step(lbeh_handle *h, Ctx &c, bool capture, cudaGraphConditionalHandl
     c.ncur ^= 1;
   }
   if (c.solids) {
+    // colloid forces and motion, then the lattice remap (Sec. II.E)
     StageTimer st(h, LBEH_STAGE_COLLOID);
     h->ops.colloid_bb(c);
+    colloid_forces_move(c);
+    if (c.moving) {
+      cudaMemcpyAsync(c.solid_old, c.solid, c.d.N, cudaMemcpyDeviceToDevice, c.s);
+      cudaMemcpyAsync(c.owner_old, c.owner, 4 * c.d.N, cudaMemcpyDeviceToDevice, c.s);
+      geometry_build(c);
+      h->ops.remap(c);
+      colloid_apply_dp(c);
+    }
   }
   return LBEH_OK;
 }
@@ -400,6 +409,14 @@ int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
   ok &= (c.cq = (double *)dalloc(h, 8 * nc)) != nullptr;
   ok &= (c.cr = (double *)dalloc(h, 8 * nc)) != nullptr;
   ok &= (c.cforce = (double *)dalloc(h, 8 * 3 * nc)) != nullptr;
+  ok &= (c.cdp = (double *)dalloc(h, 8 * 3 * nc)) != nullptr;
+  c.moving = p->colloids_move != 0 && p->ncolloid_max > 0;
+  c.rho_p = p->rho_p;
+  c.k_hertz = p->k_hertz;
+  if (c.moving) {
+    ok &= (c.solid_old = (uint8_t *)dalloc(h, N)) != nullptr;
+    ok &= (c.owner_old = (int *)dalloc(h, 4 * N)) != nullptr;
+  }
   ok &= (c.ccount = (int *)dalloc(h, 4 * nc)) != nullptr;
   ok &= (c.status = (int *)dalloc(h, sizeof(int))) != nullptr;
   c.red_len = (size_t)kRedBlocks * kObsLen + 64;

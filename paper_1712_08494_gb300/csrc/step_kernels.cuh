@@ -185,7 +185,16 @@ __global__ void __launch_bounds__(256, 3)
   const int N = int(k.d.N);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
-  if (SOL && solid[i]) return;
+  if (SOL && solid[i]) {
+    // a node covered by a moving colloid must not keep the face fluxes and
+    // velocity of the step in which it was fluid
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u_out[a * N + i] = T(0);
+    if (IONS)
+#pragma unroll
+      for (int m = 0; m < 6; ++m) flux_out[m * N + i] = T(0);
+    return;
+  }
   const int r = i / nx;
   const int x = i - r * nx;
   const int z = r / ny;
@@ -615,7 +624,8 @@ __global__ void __launch_bounds__(256) k_obs(StepK<T> k, const S *__restrict__ f
 template <typename S, typename T, int NC>
 __global__ void k_colloid_bb(StepK<T> k, const S *__restrict__ fn, const T *__restrict__ rhoF,
                              const uint8_t *__restrict__ solid, const int *__restrict__ owner,
-                             const double *__restrict__ ccx, const double *__restrict__ ccr,
+                             const uint8_t *__restrict__ surface, const T *__restrict__ qc,
+                             const T *__restrict__ phi, const double *__restrict__ ccx, const double *__restrict__ ccr,
                              const double *__restrict__ cv, double *__restrict__ cforce) {
   const int j = blockIdx.x;
   const Dims d = k.d;
@@ -636,9 +646,18 @@ __global__ void k_colloid_bb(StepK<T> k, const S *__restrict__ fn, const T *__re
     int y = ((lo[1] + int((t / cnt[0]) % cnt[1])) % d.ny + d.ny) % d.ny;
     int z = ((lo[2] + int(t / ((long long)cnt[0] * cnt[1]))) % d.nz + d.nz) % d.nz;
     long long i = site(d, x, y, z);
-    if (solid[i]) continue;
     long long nb[19];
     neighbours19(d, x, y, z, nb);
+    if (solid[i]) {
+      // electric force q_c E on the colloid's surface charge (Sec. II.E)
+      if (k.has_field && surface[i] && owner[i] == j) {
+        const double q = double(qc[i]);
+        acc[0] += q * (-0.5 * (double(phi[nb[1]]) - double(phi[nb[2]])) + double(k.Eext[0]));
+        acc[1] += q * (-0.5 * (double(phi[nb[3]]) - double(phi[nb[4]])) + double(k.Eext[1]));
+        acc[2] += q * (-0.5 * (double(phi[nb[5]]) - double(phi[nb[6]])) + double(k.Eext[2]));
+      }
+      continue;
+    }
     for (int qd = 1; qd < 19; ++qd) {
       if (!solid[nb[qd]] || owner[nb[qd]] != j) continue;
       const double cvd = cx(qd) * v[0] + cy(qd) * v[1] + cz(qd) * v[2];
@@ -664,6 +683,127 @@ __global__ void k_colloid_bb(StepK<T> k, const S *__restrict__ fn, const T *__re
     __syncthreads();
   }
   if (threadIdx.x < 3) cforce[3 * j + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+
+// ---------------------------------------------------------------- colloid remap (Sec. II.E)
+// Walks the bounding box of colloid j at its new position (margin covers one
+// lattice step of motion).  Covered nodes (solid now, fluid before) give the
+// fluid momentum sum_sigma sum_q f c_q to the colloid; uncovered nodes (fluid
+// now, solid before, previously owned by j) are refilled with the equilibrium
+// at the mean density of the neighbours that are fluid before and after, at
+// the colloid velocity, and the colloid loses that momentum.  dp[j] receives
+// the colloid's momentum change.
+template <typename S, typename T, int NC>
+__global__ void k_remap(StepK<T> k, S *__restrict__ f, const uint8_t *__restrict__ solid,
+                        const uint8_t *__restrict__ solid_old, const int *__restrict__ owner,
+                        const int *__restrict__ owner_old, const double *__restrict__ ccx,
+                        const double *__restrict__ ccr, const double *__restrict__ cv, double *__restrict__ dp) {
+  const int j = blockIdx.x;
+  const Dims d = k.d;
+  const long long N = d.N;
+  int lo[3], cnt[3];
+  const int dims[3] = {d.nx, d.ny, d.nz};
+  for (int a = 0; a < 3; ++a) {
+    const double X = ccx[3 * j + a], r = ccr[j];
+    lo[a] = int(ceil(X - r - 3.0));
+    const int hi = int(floor(X + r + 3.0));
+    cnt[a] = min(dims[a], hi - lo[a] + 1);
+  }
+  const double v[3] = {cv[3 * j], cv[3 * j + 1], cv[3 * j + 2]};
+  double acc[3] = {0, 0, 0};
+  const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
+  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int x = ((lo[0] + int(t % cnt[0])) % d.nx + d.nx) % d.nx;
+    const int y = ((lo[1] + int((t / cnt[0]) % cnt[1])) % d.ny + d.ny) % d.ny;
+    const int z = ((lo[2] + int(t / ((long long)cnt[0] * cnt[1]))) % d.nz + d.nz) % d.nz;
+    const long long i = site(d, x, y, z);
+    const bool now = solid[i], before = solid_old[i];
+    if (now && !before && owner[i] == j) {
+      // covered: fluid momentum to the colloid
+      for (int s = 0; s < NC; ++s)
+        for (int qd = 1; qd < 19; ++qd) {
+          const double fv = double(Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]));
+          acc[0] += cx(qd) * fv;
+          acc[1] += cy(qd) * fv;
+          acc[2] += cz(qd) * fv;
+        }
+    } else if (!now && before && owner_old[i] == j) {
+      // uncovered: equilibrium refill at the neighbour-mean density
+      long long nb[19];
+      neighbours19(d, x, y, z, nb);
+      double rs[2] = {0.0, 0.0};
+      int m = 0;
+      for (int qd = 1; qd < 19; ++qd) {
+        const long long jn = nb[qd];
+        if (solid[jn] || solid_old[jn]) continue;
+        ++m;
+        for (int s = 0; s < NC; ++s)
+          for (int q2 = 0; q2 < 19; ++q2)
+            rs[s] += double(Store<S, T>::ld(f, (size_t)(s * 19 + q2) * N + jn, wq<T>(q2) * k.shift[s]));
+      }
+      const double usq = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+      for (int s = 0; s < NC; ++s) {
+        const double rb = m > 0 ? rs[s] / double(m) : 0.0;
+        for (int qd = 0; qd < 19; ++qd) {
+          const double cu = cx(qd) * v[0] + cy(qd) * v[1] + cz(qd) * v[2];
+          const double feq = wq<double>(qd) * rb * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
+          Store<S, T>::st(f, (size_t)(s * 19 + qd) * N + i, T(feq), wq<T>(qd) * k.shift[s]);
+        }
+        acc[0] -= rb * v[0];
+        acc[1] -= rb * v[1];
+        acc[2] -= rb * v[2];
+      }
+    }
+  }
+  __shared__ double sh[3][256];
+  for (int a = 0; a < 3; ++a) sh[a][threadIdx.x] = acc[a];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int a = 0; a < 3; ++a) sh[a][threadIdx.x] += sh[a][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) dp[3 * j + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+// Ions of covered nodes go in equal shares to their D3Q19 neighbours that are
+// fluid before and after the move (gathered by the receivers, fixed order).
+template <typename T>
+__global__ void __launch_bounds__(256) k_remap_ions(StepK<T> k, T *__restrict__ n, const uint8_t *__restrict__ solid,
+                                                    const uint8_t *__restrict__ solid_old) {
+  const Dims d = k.d;
+  const long long N = d.N;
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  if (solid[i] || solid_old[i]) return;
+  int x, y, z;
+  coords(d, i, x, y, z);
+  long long nb[19];
+  neighbours19(d, x, y, z, nb);
+  T add[2] = {T(0), T(0)};
+  for (int qd = 1; qd < 19; ++qd) {
+    const long long src = nb[opp(qd)];  // node i - c_q sends along c_q to i
+    if (!(solid[src] && !solid_old[src])) continue;
+    int sx, sy, sz;
+    coords(d, src, sx, sy, sz);
+    long long sn[19];
+    neighbours19(d, sx, sy, sz, sn);
+    int m = 0;
+    for (int q2 = 1; q2 < 19; ++q2) m += (!solid[sn[q2]] && !solid_old[sn[q2]]) ? 1 : 0;
+    if (m == 0) continue;
+    for (int s = 0; s < 2; ++s) add[s] += n[s * N + src] / T(m);
+  }
+  n[i] += add[0];
+  n[N + i] += add[1];
+}
+
+template <typename T>
+__global__ void k_zero_solid_ions(T *__restrict__ n, const uint8_t *__restrict__ solid, long long N) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= N || !solid[i]) return;
+  n[i] = T(0);
+  n[N + i] = T(0);
 }
 
 // ---------------------------------------------------------------- host launchers
@@ -765,14 +905,32 @@ template <typename S, typename T> struct Launch {
     auto k = make_stepk<T>(c);
     const S *fn = (const S *)c.f[c.cur];
     if (c.ncomp == 2)
-      count_launch(), k_colloid_bb<S, T, 2><<<c.ncoll, B, 0, c.s>>>(k, fn, (const T *)c.rho, c.solid, c.owner, c.cx, c.cr, c.cv,
-                                                    c.cforce);
+      count_launch(), k_colloid_bb<S, T, 2><<<c.ncoll, B, 0, c.s>>>(
+          k, fn, (const T *)c.rho, c.solid, c.owner, c.surface, (const T *)c.qc, (const T *)c.phit, c.cx, c.cr, c.cv,
+          c.cforce);
     else
-      count_launch(), k_colloid_bb<S, T, 1><<<c.ncoll, B, 0, c.s>>>(k, fn, (const T *)c.rho, c.solid, c.owner, c.cx, c.cr, c.cv,
-                                                    c.cforce);
+      count_launch(), k_colloid_bb<S, T, 1><<<c.ncoll, B, 0, c.s>>>(
+          k, fn, (const T *)c.rho, c.solid, c.owner, c.surface, (const T *)c.qc, (const T *)c.phit, c.cx, c.cr, c.cv,
+          c.cforce);
+  }
+  static void remap(Ctx &c) {
+    auto k = make_stepk<T>(c);
+    S *f = (S *)c.f[c.cur];
+    if (c.ncomp == 2)
+      count_launch(), k_remap<S, T, 2><<<c.ncoll, B, 0, c.s>>>(k, f, c.solid, c.solid_old, c.owner, c.owner_old, c.cx,
+                                                                c.cr, c.cv, c.cdp);
+    else
+      count_launch(), k_remap<S, T, 1><<<c.ncoll, B, 0, c.s>>>(k, f, c.solid, c.solid_old, c.owner, c.owner_old, c.cx,
+                                                                c.cr, c.cv, c.cdp);
+    if (c.nions) {
+      T *n = (T *)c.n[c.ncur];
+      count_launch(), k_remap_ions<T><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, n, c.solid, c.solid_old);
+      count_launch(), k_zero_solid_ions<T><<<grid_for(c.d.N, B), B, 0, c.s>>>(n, c.solid, c.d.N);
+    }
   }
   static PrecOps ops() {
     PrecOps o;
+    o.remap = remap;
     o.init_eq = init_eq;
     o.init_f = init_f;
     o.get_f = get_f;

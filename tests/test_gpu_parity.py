@@ -102,8 +102,9 @@ def test_fp64_single_component_fixed_colloids(lbeh):
     errs = compare(sg, so)
     assert all(e < 1e-11 for e in errs.values()), errs
     cf = sg.get(("rho",))["cf"]
-    # momentum exchange of the last step vs the oracle's bounce-back sum
-    assert rel_err(cf, so.p_bb) < 1e-9
+    # total colloid force of the last step: bounce-back momentum exchange,
+    # electric force on the surface charge, pair forces
+    assert rel_err(cf, so.colloid_force) < 1e-9
     sg.close()
 
 
@@ -201,4 +202,73 @@ def test_fp32_modes_defect_correction_reaches_fp64_grade_residual(lbeh, prec):
     assert o.poisson_relres < 1e-11
     errs = compare(sg, so, ("phi",))
     assert errs["phi"] < 2e-4, errs
+    sg.close()
+
+
+# ---------------------------------------------------------------- moving colloids
+def _moving(n=16, ncomp=1, prec="fp64", X=((7.45, 8.2, 7.9),), V=((0.2, -0.15, 0.1),), R=(3.0,), Q=(-5.0,),
+            E=(1e-3, 0.0, 0.0)):
+    nc = len(R)
+    p = synth.Params(nx=n, ny=n, nz=n, ncomp=ncomp, nions=2, prec=prec, G=4.0 if ncomp == 2 else 0.0,
+                     ncolloid_max=nc, colloids_move=1, poisson_tol=1e-13, poisson_max_iter=500, E_ext=E,
+                     eps_r=(1.0, 1.0) if ncomp == 1 else (1.0, 0.5), rho0_shift=(1.0, 0.0))
+    rng = np.random.default_rng(21)
+    if ncomp == 1:
+        rho = np.ones((1, n, n, n)) * (1 + 0.01 * rng.uniform(-1, 1, size=(1, n, n, n)))
+    else:
+        z = np.arange(n)[:, None, None] * np.ones((n, n, n))
+        red = np.where(z < n // 2, 0.7, 0.04) * (1 + 0.01 * rng.uniform(-1, 1, size=(n, n, n)))
+        rho = np.stack([red, 0.74 - red])
+    ions = np.full((2, n, n, n), 0.01)
+    ions[0] += -sum(Q) / n ** 3
+    return synth.Workload("moving", p, rho, ions, np.array(X, dtype=float), np.array(V, dtype=float),
+                          np.array(Q, dtype=float), np.array(R, dtype=float))
+
+
+@pytest.mark.parametrize("ncomp", [1, 2])
+def test_fp64_moving_colloid_remap(lbeh, ncomp):
+    """Moving charged colloid in salt under a field: bounce-back with the
+    moving-wall term, velocity-Verlet, node covering/uncovering with momentum
+    and ion transfer (Sec. II.E).  The colloid crosses lattice nodes."""
+    w = _moving(ncomp=ncomp)
+    so = oracle_for(w)
+    sg = gpu_for(w, lbeh)
+    solid0 = so.solid.copy()
+    step_both(sg, so, 5)
+    assert not np.array_equal(solid0, so.solid)
+    errs = compare(sg, so)
+    assert all(e < 1e-10 for e in errs.values()), errs
+    got = sg.get(("rho",))
+    assert rel_err(got["cx"], so.cx) < 1e-13
+    assert rel_err(got["cv"], so.cv) < 1e-10
+    assert rel_err(got["cf"], so.colloid_force) < 1e-9
+    assert np.array_equal(sg.aux(lbeh.LBEH_AUX_SOLID).astype(bool), so.solid)
+    sg.close()
+
+
+def test_fp64_colliding_colloids_hertz_and_lubrication(lbeh):
+    """Two colloids in near contact approaching each other: lubrication below a
+    surface gap of 2/3 and Hertz repulsion once they overlap."""
+    w = _moving(n=20, X=((6.1, 10.0, 10.0), (12.5, 10.2, 9.9)), V=((0.08, 0.0, 0.0), (-0.08, 0.01, 0.0)),
+                R=(3.0, 3.0), Q=(-2.0, -2.0), E=(0.0, 0.0, 0.0))
+    so = oracle_for(w)
+    sg = gpu_for(w, lbeh)
+    step_both(sg, so, 4)
+    errs = compare(sg, so)
+    assert all(e < 1e-10 for e in errs.values()), errs
+    got = sg.get(("rho",))
+    assert rel_err(got["cx"], so.cx) < 1e-13
+    assert rel_err(got["cv"], so.cv) < 1e-10
+    sg.close()
+
+
+def test_fp32_suspension_runs_and_conserves_ions(lbeh):
+    w = synth.suspension(n=32, ncoll=3, r=4.0, prec="fp32", tol=1e-6, Ex=1e-3)
+    sg = gpu_for(w, lbeh)
+    o0 = sg.observables()
+    assert sg.step(20) == lbeh.LBEH_OK
+    o1 = sg.observables()
+    assert abs(o1.ions[0] - o0.ions[0]) < 1e-5 * o0.ions[0]
+    assert abs(o1.ions[1] - o0.ions[1]) < 1e-5 * o0.ions[1]
+    assert np.isfinite(o1.colloid_v).all()
     sg.close()
