@@ -206,7 +206,45 @@ int lbeh_observables_noalloc(int nx, int ny, int nz, int ncomp, int nions, int d
                              const void *n, const uint8_t *solid, const double *qc, lbeh_obs *out,
                              void *stream);
 
-/* Release all device state. */
+/* Batches of independent systems (the model of Sec. II on each, no coupling
+ * between them), for parameter sweeps over many small boxes of uneven size.
+ *
+ * lbeh_create_batch allocates nbox systems, box b from per_box[b].  All boxes
+ * share prec (LBEH_FP64 or LBEH_FP32), ncomp, nions and stream, and carry no
+ * colloids (ncolloid_max = 0); each box's Poisson multigrid levels above its
+ * coarse tail must have even extents (edges divisible by 8 suffice).
+ * Errors: INVALID_ARG (mismatched or bad parameters), UNSUPPORTED (other
+ * precisions, odd levels, no feasible launch shape), OOM, CUDA.
+ *
+ * lbeh_batch_box returns a handle to box b that the batch owns (valid until
+ * lbeh_destroy of the batch; lbeh_destroy on it does nothing).  Load, read and
+ * observe each box through it with lbeh_set_fields / lbeh_get_fields /
+ * lbeh_get_aux / lbeh_observables; lbeh_step on it advances that box alone
+ * with the single-system kernels.  Those calls on the batch handle itself
+ * return INVALID_ARG.
+ *
+ * lbeh_step on the batch handle advances every box by nsteps with one
+ * kernel launch, replayed from a CUDA graph: one thread-block cluster per
+ * box runs the whole coupled step for all nsteps, separated by cluster
+ * barriers.  lbeh_batch_step_sequential runs the same kernel once per box, in
+ * box order; with the same launch shape the two give bitwise-identical
+ * states.  Both synchronise the stream and return the first error status over
+ * the boxes (each box keeps its own in lbeh_observables).
+ *
+ * The launch shape is the number of blocks (of 512 threads) per cluster, one
+ * of 1, 2, 4, 8, 16.  lbeh_batch_tune times every feasible shape on
+ * probe_steps steps from the current state (restored after each trial, so
+ * the boxes' states are unchanged), keeps the fastest and reports it and its
+ * time per step in ms.  lbeh_batch_set_shape fixes a shape (UNSUPPORTED if it
+ * cannot launch); lbeh_batch_shape returns the current one. */
+int lbeh_create_batch(const lbeh_params *per_box, int nbox, lbeh_handle **out);
+int lbeh_batch_box(lbeh_handle *batch, int b, lbeh_handle **box);
+int lbeh_batch_step_sequential(lbeh_handle *batch, int nsteps);
+int lbeh_batch_tune(lbeh_handle *batch, int probe_steps, int *cluster_blocks, double *ms_per_step);
+int lbeh_batch_set_shape(lbeh_handle *batch, int cluster_blocks);
+int lbeh_batch_shape(lbeh_handle *batch);
+
+/* Release all device state (a batch releases its boxes). */
 void lbeh_destroy(lbeh_handle *h);
 
 /* Text of the last CUDA failure seen by the handle (empty if none); owned by

@@ -38,22 +38,26 @@ __host__ __device__ constexpr T wq(int q) {
 template <typename S, typename T> struct Store;
 template <typename T> struct Store<double, T> {
   __device__ static T ld(const double *p, size_t i, T) { return T(p[i]); }
+  __device__ static T ldc(const double *p, size_t i, T) { return T(p[i]); }
   __device__ static void st(double *p, size_t i, T v, T) { p[i] = double(v); }
 };
 template <typename T> struct Store<float, T> {
   __device__ static T ld(const float *p, size_t i, T) { return T(__ldg(p + i)); }
+  __device__ static T ldc(const float *p, size_t i, T) { return T(p[i]); }
   __device__ static void st(float *p, size_t i, T v, T) { p[i] = float(v); }
 };
 template <typename T> struct Store<__nv_bfloat16, T> {
   __device__ static T ld(const __nv_bfloat16 *p, size_t i, T shift) {
     return T(__bfloat162float(p[i])) + shift;
   }
+  __device__ static T ldc(const __nv_bfloat16 *p, size_t i, T shift) { return ld(p, i, shift); }
   __device__ static void st(__nv_bfloat16 *p, size_t i, T v, T shift) {
     p[i] = __float2bfloat16_rn(float(v - shift));
   }
 };
 template <typename T> struct Store<__half, T> {
   __device__ static T ld(const __half *p, size_t i, T shift) { return T(__half2float(p[i])) + shift; }
+  __device__ static T ldc(const __half *p, size_t i, T shift) { return ld(p, i, shift); }
   __device__ static void st(__half *p, size_t i, T v, T shift) { p[i] = __float2half_rn(float(v - shift)); }
 };
 

@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <atomic>
+#include <utility>
+#include <vector>
 
 #include "common.cuh"
 
@@ -121,8 +123,45 @@ int poisson_capture(Poisson *p, Ctx &c, cudaGraphConditionalHandle handle);
 int poisson_read(Poisson *p, cudaStream_t s, PoissonStats *out);
 // false when the whole solve is one cooperative launch (no conditional node)
 bool poisson_needs_conditional(const Poisson *p);
+// Arguments of the whole solve of this system by one team of blocks (the
+// batched step): writes PArgs<double> (FP64) or PArgs<float> (double-float
+// potential) into `out` (out_bytes must match) and returns the dynamic shared
+// memory of the tail cycle, or -1 when the level structure needs the
+// multi-kernel solve.
+long long poisson_team_args(Poisson *p, const Ctx &c, void *out, size_t out_bytes);
+// Device buffers the solve carries from step to step (previous solution,
+// solver state): (pointer, bytes) pairs.
+void poisson_state_buffers(Poisson *p, const Ctx &c, std::vector<std::pair<void *, size_t>> &out);
 void phi_to_double(Ctx &c, double *out);       // FP64 values of the potential
 void phi_from_double(Ctx &c, const double *in);
+
+// Batched step (batch.cu; kernels in batch_<prec>.cu).
+struct BatchBox {
+  Ctx *c;
+  Poisson *pois;  // null: no potential
+};
+struct BatchKernels {
+  size_t rec_bytes = 0;                                // device record of one system
+  long long (*fill)(const BatchBox &, void *rec) = nullptr;  // tail shared memory, or -1
+  const void *(*kernel)(int ncomp, int nions) = nullptr;
+};
+BatchKernels batch_kernels_f64();
+BatchKernels batch_kernels_f32();
+struct Batch;
+// Boxes share precision (FP64 or FP32), ncomp, nions and stream; their status
+// words are moved into one array owned by the batch.  rc receives the error.
+Batch *batch_create(const std::vector<BatchBox> &boxes, cudaStream_t s, int *rc);
+void batch_destroy(Batch *b);
+// nsteps steps of every box: one graph-launched kernel (sequential = false) or
+// one launch per box in box order.  Flips the boxes' parities; returns the
+// first non-zero device status word over the boxes (0 when all are clear).
+int batch_step(Batch *b, int nsteps, bool sequential, int *first_status);
+int batch_set_shape(Batch *b, int cluster_blocks);  // LBEH_OK or LBEH_ERR_UNSUPPORTED
+int batch_shape(const Batch *b);
+int batch_box_status(const Batch *b, int box);  // status word of a box read by the last batch_step
+// Times each feasible cluster size on probe_steps steps (state restored after
+// each) and keeps the fastest.
+int batch_tune(Batch *b, int probe_steps, int *best_blocks, double *best_ms_per_step);
 
 // Deterministic FP64 reductions (reduce.cu).
 void reduce_partials_final(const double *partials, int nblocks, int len, double *out, cudaStream_t s);
@@ -130,5 +169,15 @@ double dot_f64(const double *a, const double *b, long long n, double *scratch, c
 double sum_f64(const double *a, long long n, double *scratch, cudaStream_t s);
 
 inline int grid_for(long long n, int block) { return int((n + block - 1) / block); }
+
+// Raise (never lower) a kernel's dynamic shared-memory limit: the limit is a
+// property of the kernel shared by every system in the process, so a smaller
+// system created later must not shrink what an earlier one launches with.
+inline bool raise_smem_limit(const void *fn, size_t bytes) {
+  cudaFuncAttributes a{};
+  if (cudaFuncGetAttributes(&a, fn) != cudaSuccess) return false;
+  if ((size_t)a.maxDynamicSharedSizeBytes >= bytes) return true;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
+}
 
 }  // namespace lbeh

@@ -48,6 +48,11 @@ struct lbeh_handle {
   bool eager = false;                  // LBEH_EAGER=1 disables graphs
   int graph_launches = 0;              // kernels per replay outside the Poisson cycles
   long long total_iters_seen = 0;      // Poisson cycles already accounted
+  // batches: the batch handle owns its boxes; a box points back to its batch
+  Batch *batch = nullptr;
+  std::vector<lbeh_handle *> boxes;
+  lbeh_handle *parent = nullptr;
+  bool stats_stale = false;  // Poisson statistics not read back since a batched step
 };
 
 std::atomic<long long> lbeh::g_launches{0};
@@ -459,6 +464,72 @@ int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
   return LBEH_OK;
 }
 
+static int batch_advance(lbeh_handle *h, int nsteps, bool sequential);
+
+int lbeh_create_batch(const lbeh_params *per_box, int nbox, lbeh_handle **out) {
+  if (!out) return LBEH_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!per_box || nbox < 1) return LBEH_ERR_INVALID_ARG;
+  for (int b = 0; b < nbox; ++b) {
+    const lbeh_params &p = per_box[b];
+    if (p.stream != per_box[0].stream || p.prec != per_box[0].prec || p.ncomp != per_box[0].ncomp ||
+        p.nions != per_box[0].nions || p.ncolloid_max != 0)
+      return LBEH_ERR_INVALID_ARG;
+    const int rc = check_params(&p);
+    if (rc) return rc;
+  }
+  if (per_box[0].prec != LBEH_FP64 && per_box[0].prec != LBEH_FP32) return LBEH_ERR_UNSUPPORTED;
+  lbeh_handle *h = new (std::nothrow) lbeh_handle;
+  if (!h) return LBEH_ERR_OOM;
+  h->p = per_box[0];
+  h->c.s = (cudaStream_t)per_box[0].stream;
+  std::vector<BatchBox> boxes;
+  int rc = LBEH_OK;
+  for (int b = 0; b < nbox && rc == LBEH_OK; ++b) {
+    lbeh_handle *bx = nullptr;
+    rc = lbeh_create(&per_box[b], &bx);
+    if (rc != LBEH_OK) break;
+    bx->parent = h;
+    h->boxes.push_back(bx);
+    boxes.push_back(BatchBox{&bx->c, bx->pois});
+  }
+  if (rc == LBEH_OK) h->batch = batch_create(boxes, h->c.s, &rc);
+  if (rc != LBEH_OK || !h->batch) {
+    lbeh_destroy(h);
+    return rc != LBEH_OK ? rc : LBEH_ERR_CUDA;
+  }
+  *out = h;
+  return LBEH_OK;
+}
+
+int lbeh_batch_box(lbeh_handle *h, int b, lbeh_handle **box) {
+  if (!h || !box || !h->batch || b < 0 || b >= (int)h->boxes.size()) return LBEH_ERR_INVALID_ARG;
+  *box = h->boxes[b];
+  return LBEH_OK;
+}
+
+int lbeh_batch_step_sequential(lbeh_handle *h, int nsteps) {
+  if (!h || !h->batch || nsteps < 0) return LBEH_ERR_INVALID_ARG;
+  return batch_advance(h, nsteps, true);
+}
+
+int lbeh_batch_set_shape(lbeh_handle *h, int cluster_blocks) {
+  if (!h || !h->batch) return LBEH_ERR_INVALID_ARG;
+  return batch_set_shape(h->batch, cluster_blocks);
+}
+
+int lbeh_batch_shape(lbeh_handle *h) {
+  if (!h || !h->batch) return LBEH_ERR_INVALID_ARG;
+  return batch_shape(h->batch);
+}
+
+int lbeh_batch_tune(lbeh_handle *h, int probe_steps, int *cluster_blocks, double *ms_per_step) {
+  if (!h || !h->batch || probe_steps < 1) return LBEH_ERR_INVALID_ARG;
+  for (lbeh_handle *bx : h->boxes)
+    if (!bx->loaded) return LBEH_ERR_INVALID_ARG;
+  return batch_tune(h->batch, probe_steps, cluster_blocks, ms_per_step);
+}
+
 int lbeh_profile_enable(lbeh_handle *h, int on) {
   if (!h) return LBEH_ERR_INVALID_ARG;
   flush_marks(h);
@@ -484,8 +555,21 @@ int lbeh_profile_read(lbeh_handle *h, lbeh_profile *out) {
   return cudaGetLastError() == cudaSuccess ? LBEH_OK : LBEH_ERR_CUDA;
 }
 
+static void destroy_handle(lbeh_handle *h);
+
 void lbeh_destroy(lbeh_handle *h) {
-  if (!h) return;
+  if (!h || h->parent) return;  // boxes of a batch go with their batch
+  if (h->batch || !h->boxes.empty()) {
+    if (h->c.s) cudaStreamSynchronize(h->c.s);
+    batch_destroy(h->batch);
+    for (lbeh_handle *bx : h->boxes) destroy_handle(bx);
+    delete h;
+    return;
+  }
+  destroy_handle(h);
+}
+
+static void destroy_handle(lbeh_handle *h) {
   if (h->c.s) cudaStreamSynchronize(h->c.s);
   flush_marks(h);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
@@ -503,6 +587,7 @@ void lbeh_destroy(lbeh_handle *h) {
 
 int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
   if (!h || !in) return LBEH_ERR_INVALID_ARG;
+  if (h->batch) return LBEH_ERR_INVALID_ARG;
   if (in->dtype != LBEH_F64 && in->dtype != LBEH_F32) return LBEH_ERR_INVALID_ARG;
   Ctx &c = h->c;
   const long long N = c.d.N;
@@ -607,8 +692,29 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
   return LBEH_OK;
 }
 
+static int batch_advance(lbeh_handle *h, int nsteps, bool sequential) {
+  for (lbeh_handle *bx : h->boxes)
+    if (!bx->loaded) return LBEH_ERR_INVALID_ARG;
+  int st = 0;
+  const int rc = batch_step(h->batch, nsteps, sequential, &st);
+  if (rc != LBEH_OK) return cuda_fail(h, "batched step");
+  for (size_t i = 0; i < h->boxes.size(); ++i) {
+    lbeh_handle *bx = h->boxes[i];
+    bx->steps += nsteps;
+    bx->stats_stale = true;
+    const int dst = batch_box_status(h->batch, (int)i);
+    if (dst & ST_POISSON) bx->status = LBEH_ERR_POISSON_NOT_CONVERGED;
+    if (dst & ST_TIMEOUT) bx->status = LBEH_ERR_BARRIER_TIMEOUT;
+  }
+  h->steps += nsteps;
+  if (st & ST_TIMEOUT) return LBEH_ERR_BARRIER_TIMEOUT;
+  if (st & ST_POISSON) return LBEH_ERR_POISSON_NOT_CONVERGED;
+  return LBEH_OK;
+}
+
 int lbeh_step(lbeh_handle *h, int nsteps) {
   if (!h || nsteps < 0) return LBEH_ERR_INVALID_ARG;
+  if (h->batch) return batch_advance(h, nsteps, false);
   if (!h->loaded) return LBEH_ERR_INVALID_ARG;
   Ctx &c = h->c;
   if (nsteps == 0) return h->status;
@@ -650,6 +756,7 @@ int lbeh_step(lbeh_handle *h, int nsteps) {
     int dst = 0;
     cudaMemcpy(&dst, c.status, sizeof(int), cudaMemcpyDeviceToHost);
     if (dst & ST_POISSON) h->status = LBEH_ERR_POISSON_NOT_CONVERGED;
+    if (dst & ST_TIMEOUT) h->status = LBEH_ERR_BARRIER_TIMEOUT;
   }
   if (cudaPeekAtLastError() != cudaSuccess) return cuda_fail(h, "step");
   return h->status;
@@ -659,6 +766,7 @@ const char *lbeh_last_error(lbeh_handle *h) { return h ? h->last_error : "no han
 
 int lbeh_observables(lbeh_handle *h, lbeh_obs *out) {
   if (!h || !out) return LBEH_ERR_INVALID_ARG;
+  if (h->batch) return LBEH_ERR_INVALID_ARG;
   Ctx &c = h->c;
   std::memset(out, 0, sizeof(*out));
   h->ops.obs_partials(c, c.red, kRedBlocks);
@@ -667,6 +775,8 @@ int lbeh_observables(lbeh_handle *h, lbeh_obs *out) {
   double v[kObsLen];
   cudaMemcpyAsync(v, res, sizeof(v), cudaMemcpyDeviceToHost, c.s);
   if (cudaStreamSynchronize(c.s) != cudaSuccess) return LBEH_ERR_CUDA;
+  for (int m = 0; m < kObsLen; ++m)
+    if (!std::isfinite(v[m])) h->status = LBEH_ERR_NONFINITE;
   out->mass[0] = v[0];
   out->mass[1] = v[1];
   out->ions[0] = v[2];
@@ -687,6 +797,15 @@ int lbeh_observables(lbeh_handle *h, lbeh_obs *out) {
     for (int j = 0; j < c.ncoll; ++j)
       for (int a = 0; a < 3; ++a) out->colloid_v[a] += cv[3 * j + a] / c.ncoll;
   }
+  if (h->stats_stale && h->pois) {
+    PoissonStats ps;
+    if (poisson_read(h->pois, c.s, &ps) == 0) {
+      h->last_iters = ps.iters;
+      h->last_relres = ps.relres;
+      h->total_iters_seen = ps.total_iters;
+    }
+    h->stats_stale = false;
+  }
   out->poisson_relres = h->last_relres;
   out->poisson_iters = h->last_iters;
   out->status = h->status;
@@ -696,6 +815,7 @@ int lbeh_observables(lbeh_handle *h, lbeh_obs *out) {
 
 int lbeh_get_fields(lbeh_handle *h, lbeh_fields *out) {
   if (!h || !out) return LBEH_ERR_INVALID_ARG;
+  if (h->batch) return LBEH_ERR_INVALID_ARG;
   if (out->dtype != LBEH_F64 && out->dtype != LBEH_F32) return LBEH_ERR_INVALID_ARG;
   Ctx &c = h->c;
   const long long N = c.d.N;

@@ -22,116 +22,14 @@
 #include <algorithm>
 #include <type_traits>
 #include <cmath>
+#include <cstring>
 #include <utility>
 #include <vector>
 
 #include "internal.h"
+#include "poisson_dev.cuh"
 
 namespace lbeh {
-
-constexpr long long kTailCells = 512;
-constexpr size_t kTailSmem = 200 * 1024;
-constexpr int kMaxLevels = 16;
-constexpr int kNu = 2;  // pre- and post-smoothing sweeps
-
-template <typename T> struct Level {
-  int nx = 0, ny = 0, nz = 0;
-  long long N = 0;
-  int cf[3] = {0, 0, 0};  // coarsened along x, y, z relative to the finer level
-  T h[3] = {T(1), T(1), T(1)};  // 1 / H_a^2
-  T *k[3] = {nullptr, nullptr, nullptr};
-  T *x = nullptr, *x2 = nullptr, *b = nullptr;
-  const T *eps = nullptr;  // set: face coefficients (eps_i + eps_{i+a})/2 formed from eps, k unused
-  bool rb = false;
-  __host__ __device__ Dims dims() const { return Dims{nx, ny, nz, N}; }
-};
-
-// face coefficients k_a(i) (p: +a face) and k_a(i-a) (m) of a cell
-template <typename T> struct Faces {
-  T xp, xm, yp, ym, zp, zm;
-};
-template <typename T>
-__device__ __forceinline__ Faces<T> faces(const Level<T> &L, long long i, long long ixp, long long ixm, long long iyp,
-                                          long long iym, long long izp, long long izm) {
-  Faces<T> f;
-  if (L.eps) {
-    const T e = L.eps[i];
-    f.xp = T(0.5) * (e + L.eps[ixp]);
-    f.xm = T(0.5) * (L.eps[ixm] + e);
-    f.yp = T(0.5) * (e + L.eps[iyp]);
-    f.ym = T(0.5) * (L.eps[iym] + e);
-    f.zp = T(0.5) * (e + L.eps[izp]);
-    f.zm = T(0.5) * (L.eps[izm] + e);
-  } else {
-    f.xp = L.k[0][i];
-    f.xm = L.k[0][ixm];
-    f.yp = L.k[1][i];
-    f.ym = L.k[1][iym];
-    f.zp = L.k[2][i];
-    f.zm = L.k[2][izm];
-  }
-  return f;
-}
-
-template <typename T> struct Tail {
-  int n = 0;
-  Level<T> L[kMaxLevels];
-};
-
-// Double-float numbers (hi + lo, two FP32 words, ~48-bit significand) with
-// error-free transformations: the FP32 modes keep the potential and form the
-// defect-correction residual in this form, on the FP32 pipes (the FP64 rate
-// of the target is a small fraction of its FP32 rate).  Intrinsics keep the
-// compiler from contracting the compensated sums.
-struct DF {
-  float hi, lo;
-};
-__device__ __forceinline__ DF two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return DF{s, e};
-}
-__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-  DF s = two_sum(a.hi, b.hi);
-  const DF t = two_sum(a.lo, b.lo);
-  s.lo = __fadd_rn(s.lo, t.hi);
-  s = fast_two_sum(s.hi, s.lo);
-  s.lo = __fadd_rn(s.lo, t.lo);
-  return fast_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, DF{-b.hi, -b.lo}); }
-__device__ __forceinline__ DF df_mul_f(DF a, float b) {
-  const float p = __fmul_rn(a.hi, b);
-  float e = __fmaf_rn(a.hi, b, -p);
-  e = __fmaf_rn(a.lo, b, e);
-  return fast_two_sum(p, e);
-}
-__device__ __forceinline__ DF df_mul(DF a, DF b) {
-  const float p = __fmul_rn(a.hi, b.hi);
-  float e = __fmaf_rn(a.hi, b.hi, -p);
-  e = __fmaf_rn(a.hi, b.lo, e);
-  e = __fmaf_rn(a.lo, b.hi, e);
-  return fast_two_sum(p, e);
-}
-__host__ __device__ inline DF df_split(double v) {
-  const float h = float(v);
-  return DF{h, float(v - double(h))};
-}
-
-// Device-side solver state.
-struct PDev {
-  double mean_q, mean_phi, bnorm2, rnorm2, relres, tol;
-  DF mean_q_df, mean_phi_df;
-  int iters, max_iter, cond, notconv;
-  long long total_iters;
-  int have_prev;  // phi_prev holds the solution of the previous step
-  int zero;       // right-hand side vanishes: phi = 0
-};
 
 struct Bar;
 struct Poisson {
@@ -150,109 +48,6 @@ struct Poisson {
   std::vector<void *> allocs;
   int body_launches = 0;      // kernels of one cycle (launch accounting in graphs)
 };
-
-// ---------------------------------------------------------------- level operations
-template <typename T>
-__device__ __forceinline__ void stencil(const Dims &d, const Level<T> &L, long long i, int x, int y, int z,
-                                        const T *__restrict__ xv, T &off, T &diag) {
-  const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
-  const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
-  const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
-  const Faces<T> f = faces(L, i, ixp, ixm, iyp, iym, izp, izm);
-  const T kxp = f.xp, kxm = f.xm, kyp = f.yp, kym = f.ym, kzp = f.zp, kzm = f.zm;
-  off = L.h[0] * (kxp * xv[ixp] + kxm * xv[ixm]) + L.h[1] * (kyp * xv[iyp] + kym * xv[iym]) +
-        L.h[2] * (kzp * xv[izp] + kzm * xv[izm]);
-  diag = L.h[0] * (kxp + kxm) + L.h[1] * (kyp + kym) + L.h[2] * (kzp + kzm);
-}
-
-// one colour of a red-black sweep over the thread range t0, t0+dt, ... < N/2
-template <typename T>
-__device__ __forceinline__ void rb_range(const Level<T> &L, int color, long long t0, long long dt) {
-  const Dims d = L.dims();
-  const unsigned hx = unsigned(d.nx / 2);
-  for (long long t = t0; t < d.N / 2; t += dt) {
-    const unsigned r = unsigned(t) / hx;
-    const int xh = int(unsigned(t) - r * hx);
-    const int z = int(r / unsigned(d.ny));
-    const int y = int(r - unsigned(z) * unsigned(d.ny));
-    const int x = 2 * xh + ((y + z + color) & 1);
-    const long long i = site(d, x, y, z);
-    T off, diag;
-    stencil(d, L, i, x, y, z, L.x, off, diag);
-    L.x[i] = (off - L.b[i]) / diag;
-  }
-}
-
-template <typename T>
-__device__ __forceinline__ void jacobi_range(const Level<T> &L, T w, long long t0, long long dt) {
-  const Dims d = L.dims();
-  for (long long i = t0; i < d.N; i += dt) {
-    int x, y, z;
-    coords(d, i, x, y, z);
-    T off, diag;
-    stencil(d, L, i, x, y, z, L.x, off, diag);
-    L.x2[i] = L.x[i] + w * ((off - L.b[i]) / diag - L.x[i]);
-  }
-}
-
-// coarse b(I) = mean over children of the fine residual (b - A x)
-template <typename T>
-__device__ __forceinline__ void restrict_range(const Level<T> &F, const Level<T> &C, long long t0, long long dt) {
-  const Dims f = F.dims(), c = C.dims();
-  for (long long I = t0; I < c.N; I += dt) {
-    int X, Y, Z;
-    coords(c, I, X, Y, Z);
-    T acc = T(0);
-    int cnt = 0;
-    for (int tz = 0; tz <= C.cf[2]; ++tz)
-      for (int ty = 0; ty <= C.cf[1]; ++ty)
-        for (int tx = 0; tx <= C.cf[0]; ++tx) {
-          const int x = C.cf[0] ? 2 * X + tx : X, y = C.cf[1] ? 2 * Y + ty : Y, z = C.cf[2] ? 2 * Z + tz : Z;
-          const long long i = site(f, x, y, z);
-          T off, diag;
-          stencil(f, F, i, x, y, z, F.x, off, diag);
-          acc += F.b[i] - (off - diag * F.x[i]);
-          ++cnt;
-        }
-    C.b[I] = acc / T(cnt);
-  }
-}
-
-// trilinear (cell-centred) prolongation and correction x_f += P x_c
-template <typename T>
-__device__ __forceinline__ void prolong_range(const Level<T> &F, const Level<T> &C, long long t0, long long dt) {
-  const Dims f = F.dims(), c = C.dims();
-  const int cd[3] = {c.nx, c.ny, c.nz};
-  for (long long i = t0; i < f.N; i += dt) {
-    int x, y, z;
-    coords(f, i, x, y, z);
-    const int p[3] = {x, y, z};
-    int I0[3], I1[3];
-    T w0[3], w1[3];
-    for (int a = 0; a < 3; ++a) {
-      if (C.cf[a]) {
-        const int I = p[a] >> 1;
-        I0[a] = I;
-        I1[a] = (p[a] & 1) ? (I + 1 == cd[a] ? 0 : I + 1) : (I == 0 ? cd[a] - 1 : I - 1);
-        w0[a] = T(0.75);
-        w1[a] = T(0.25);
-      } else {
-        I0[a] = I1[a] = p[a];
-        w0[a] = T(1);
-        w1[a] = T(0);
-      }
-    }
-    T acc = T(0);
-    for (int tz = 0; tz < 2; ++tz)
-      for (int ty = 0; ty < 2; ++ty)
-        for (int tx = 0; tx < 2; ++tx) {
-          const T w = (tx ? w1[0] : w0[0]) * (ty ? w1[1] : w0[1]) * (tz ? w1[2] : w0[2]);
-          if (w == T(0)) continue;
-          acc += w * C.x[site(c, tx ? I1[0] : I0[0], ty ? I1[1] : I0[1], tz ? I1[2] : I0[2])];
-        }
-    F.x[i] += acc;
-  }
-}
 
 // ---------------------------------------------------------------- multi-block kernels
 template <typename T> __global__ void k_rb(Level<T> L, int color) {
@@ -309,122 +104,6 @@ template <typename T> __global__ void k_coef_coarsen(Level<T> F, Level<T> C) {
         ++cnt;
       }
     C.k[a][I] = acc / T(cnt);
-  }
-}
-
-// ---------------------------------------------------------------- single-block tail
-template <typename T> __device__ void tail_smooth(const Level<T> &L, int sweeps) {
-  for (int s = 0; s < sweeps; ++s) {
-    if (L.rb) {
-      rb_range(L, 0, threadIdx.x, blockDim.x);
-      __syncthreads();
-      rb_range(L, 1, threadIdx.x, blockDim.x);
-      __syncthreads();
-    } else {
-      jacobi_range(L, T(0.8), threadIdx.x, blockDim.x);
-      __syncthreads();
-      for (long long i = threadIdx.x; i < L.N; i += blockDim.x) L.x[i] = L.x2[i];
-      __syncthreads();
-    }
-  }
-}
-
-// Shared-memory bytes of the tail levels first..n-1 (three face arrays, x, b,
-// and x2 where an axis is odd).
-template <typename T> __host__ __device__ inline size_t tail_bytes(const Tail<T> &tl, int first) {
-  size_t b = 0;
-  for (int l = first; l < tl.n; ++l) b += size_t(tl.L[l].rb ? 5 : 6) * tl.L[l].N * sizeof(T);
-  return b;
-}
-
-// V-cycle over levels first..n-1 of `tl` inside one block, with every level
-// held in shared memory: face coefficients and the right-hand side of level
-// `first` are loaded, the correction x of level `first` is written back.
-// V-cycle over levels first..n-1 of lv inside one block, every level held in
-// shared memory (descriptors included): face coefficients and the right-hand
-// side of level `first` are loaded, its correction x is written back.
-template <typename T>
-__device__ void tail_vcycle(const Level<T> *__restrict__ lv, int n, int first, unsigned char *smem_raw, T *sh) {
-  __shared__ Level<T> sl[kMaxLevels];
-  if (threadIdx.x == 0) {
-    T *p = reinterpret_cast<T *>(smem_raw);
-    for (int l = first; l < n; ++l) {
-      Level<T> L = lv[l];
-      const long long m = L.N;
-      for (int a = 0; a < 3; ++a) {
-        L.k[a] = p;
-        p += m;
-      }
-      L.x = p;
-      p += m;
-      L.b = p;
-      p += m;
-      if (!L.rb) {
-        L.x2 = p;
-        p += m;
-      }
-      L.eps = nullptr;
-      sl[l] = L;
-    }
-  }
-  __syncthreads();
-  for (int l = first; l < n; ++l) {
-    const Level<T> G = lv[l];
-    const Level<T> S = sl[l];
-    const Dims dg = G.dims();
-    for (long long i = threadIdx.x; i < G.N; i += blockDim.x) {
-      if (G.eps) {
-        int x, y, z;
-        coords(dg, i, x, y, z);
-        const T e = G.eps[i];
-        S.k[0][i] = T(0.5) * (e + G.eps[site(dg, wrapp(x, dg.nx), y, z)]);
-        S.k[1][i] = T(0.5) * (e + G.eps[site(dg, x, wrapp(y, dg.ny), z)]);
-        S.k[2][i] = T(0.5) * (e + G.eps[site(dg, x, y, wrapp(z, dg.nz))]);
-      } else {
-        for (int a = 0; a < 3; ++a) S.k[a][i] = G.k[a][i];
-      }
-      if (l == first) S.b[i] = G.b[i];
-    }
-  }
-  __syncthreads();
-  for (int l = first; l < n; ++l) {
-    const Level<T> L = sl[l];
-    if (l == n - 1) {
-      // coarsest: mean-free right-hand side, fixed relaxation count
-      T acc = T(0);
-      for (long long i = threadIdx.x; i < L.N; i += blockDim.x) acc += L.b[i];
-      sh[threadIdx.x] = acc;
-      __syncthreads();
-      for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-        __syncthreads();
-      }
-      const T mean = sh[0] / T(L.N);
-      __syncthreads();
-      for (long long i = threadIdx.x; i < L.N; i += blockDim.x) {
-        L.b[i] -= mean;
-        L.x[i] = T(0);
-      }
-      __syncthreads();
-      tail_smooth(L, L.rb ? 10 : 30);
-    } else {
-      for (long long i = threadIdx.x; i < L.N; i += blockDim.x) L.x[i] = T(0);
-      __syncthreads();
-      tail_smooth(L, kNu);
-      const Level<T> Lc = sl[l + 1];
-      restrict_range(L, Lc, threadIdx.x, blockDim.x);
-      __syncthreads();
-    }
-  }
-  for (int l = n - 2; l >= first; --l) {
-    const Level<T> Lf = sl[l], Lc = sl[l + 1];
-    prolong_range(Lf, Lc, threadIdx.x, blockDim.x);
-    __syncthreads();
-    tail_smooth(Lf, kNu);
-  }
-  {
-    const Level<T> G = lv[first], S = sl[first];
-    for (long long i = threadIdx.x; i < G.N; i += blockDim.x) G.x[i] = S.x[i];
   }
 }
 
@@ -688,400 +367,12 @@ __global__ void k_update_phi(double *__restrict__ phi, const T *__restrict__ x, 
   if (i < n) phi[i] += double(x[i]);
 }
 
-// ---------------------------------------------------------------- persistent solve
-// The whole solve in one cooperative launch: initial guess, coefficients, the
-// residual test and the defect-correction cycles, separated by grid-wide
-// barriers.  Every block evaluates the same fixed-order sums, so all blocks
-// take the same branches.  The barrier wait is bounded: a block that gives up
-// raises an abort flag and the device status, and every block then returns.
-constexpr int kPB = 512;
-constexpr long long kSpinLimit = 1LL << 24;
-constexpr double kTrustTol = 1e-8;  // FP32 residual estimate used only above this tolerance
-constexpr double kEstErr = 1e-4;    // bound of its error relative to the last exact residual  // polls of ~100 ns: about two seconds
-
-struct Bar {
-  unsigned long long arrived;  // monotonic arrival count (reset before each launch)
-  int abort, pad;
-};
-
-__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long *p, unsigned long long v) {
-  unsigned long long o;
-  asm volatile("atom.add.acq_rel.gpu.global.u64 %0, [%1], %2;" : "=l"(o) : "l"(p), "l"(v) : "memory");
-  return o;
-}
-__device__ __forceinline__ int ld_acquire_s32(const int *p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-// Grid barrier: thread 0 of every block arrives with an acquire-release add
-// on a monotonic counter (releasing the block's writes, ordered by the
-// preceding __syncthreads) and polls it with acquire loads until all blocks of
-// this round have arrived.  The wait is bounded; on time-out the block raises
-// the abort flag and the status, and every block leaves at its next barrier.
-__device__ __forceinline__ bool grid_sync(Bar *bar, int *status) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    const unsigned long long nb = gridDim.x;
-    const unsigned long long old = atom_add_acq_rel_u64(&bar->arrived, 1ull);
-    const unsigned long long target = (old / nb + 1) * nb;
-    long long spins = 0;
-    while (ld_acquire_u64(&bar->arrived) < target) {
-      if (ld_acquire_s32(&bar->abort)) break;
-      if (++spins > kSpinLimit) {
-        atomicExch(&bar->abort, 1);
-        atomicOr(status, ST_TIMEOUT);
-        break;
-      }
-      __nanosleep(20);
-    }
-    ok = !ld_acquire_s32(&bar->abort);
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
-template <typename T> struct PArgs {
-  const Level<T> *lv;                          // level table in device memory
-  int nlev;
-  int tail;                                    // first level relaxed by block 0 in shared memory
-  const T *eps, *q;
-  double *phi, *prev;                          // FP64 potential (FP64 mode)
-  float *phi_hi, *phi_lo, *prev_hi, *prev_lo;  // double-float potential (FP32 modes)
-  DF edf[3];
-  double ex, ey, ez;
-  PDev *st;
-  int *status;
-  double *part;  // [3][gridDim.x]
-  Bar *bar;
-};
-
-__device__ __forceinline__ double block_sum_n(double v, double *sh) {
-  sh[threadIdx.x] = v;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-    __syncthreads();
-  }
-  const double r = sh[0];
-  __syncthreads();
-  return r;
-}
-
-// fixed-order sum of nb partials, identical in every block
-__device__ __forceinline__ double sum_partials(const double *part, int nb, double *sh) {
-  double acc = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) acc += part[b];
-  return block_sum_n(acc, sh);
-}
-
-template <typename T, bool DFM>
-__device__ __forceinline__ void residual_site(const PArgs<T> &a, const Level<T> &L0, long long i, double qbar,
-                                              DF qbar_df, double &ar, double &ab, double &ap) {
-  const Dims d = L0.dims();
-  int x, y, z;
-  coords(d, i, x, y, z);
-  const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
-  const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
-  const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
-  const Faces<T> fc = faces(L0, i, ixp, ixm, iyp, iym, izp, izm);
-  const T kxp = fc.xp, kxm = fc.xm, kyp = fc.yp, kym = fc.ym, kzp = fc.zp, kzm = fc.zm;
-  if constexpr (DFM) {
-    const float *hi = a.phi_hi, *lo = a.phi_lo;
-    const DF p{hi[i], lo[i]};
-    DF Ap = df_mul_f(df_sub(DF{hi[ixp], lo[ixp]}, p), kxp);
-    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[ixm], lo[ixm]}, p), kxm));
-    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[iyp], lo[iyp]}, p), kyp));
-    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[iym], lo[iym]}, p), kym));
-    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[izp], lo[izp]}, p), kzp));
-    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[izm], lo[izm]}, p), kzm));
-    DF b = df_sub(qbar_df, DF{float(a.q[i]), 0.f});
-    if (a.edf[0].hi != 0.f) b = df_add(b, df_mul(a.edf[0], two_sum(kxp, -kxm)));
-    if (a.edf[1].hi != 0.f) b = df_add(b, df_mul(a.edf[1], two_sum(kyp, -kym)));
-    if (a.edf[2].hi != 0.f) b = df_add(b, df_mul(a.edf[2], two_sum(kzp, -kzm)));
-    const DF r = df_sub(b, Ap);
-    const float rf = __fadd_rn(r.hi, r.lo);
-    L0.b[i] = T(rf);
-    ar += double(rf * rf);
-    ab += double(b.hi * b.hi);
-    ap += double(p.hi);
-  } else {
-    const double *phi = a.phi;
-    const double p = phi[i];
-    double b = -(double(a.q[i]) - qbar);
-    if (a.ex != 0.0) b += a.ex * (double(kxp) - double(kxm));
-    if (a.ey != 0.0) b += a.ey * (double(kyp) - double(kym));
-    if (a.ez != 0.0) b += a.ez * (double(kzp) - double(kzm));
-    const double Ap = double(kxp) * (phi[ixp] - p) - double(kxm) * (p - phi[ixm]) + double(kyp) * (phi[iyp] - p) -
-                      double(kym) * (p - phi[iym]) + double(kzp) * (phi[izp] - p) - double(kzm) * (p - phi[izm]);
-    const double r = b - Ap;
-    L0.b[i] = T(r);
-    ar += r * r;
-    ab += b * b;
-    ap += p;
-  }
-}
-
-// residual pass + fixed-order sums in every block; returns false on abort
-template <typename T, bool DFM>
-__device__ bool residual_pass(const PArgs<T> &a, const Level<T> &L0, double qbar, DF qbar_df, double *sh,
-                              double &r2, double &b2, double &ps) {
-  const long long G = (long long)gridDim.x * blockDim.x;
-  double ar = 0.0, ab = 0.0, ap = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < L0.N; i += G)
-    residual_site<T, DFM>(a, L0, i, qbar, qbar_df, ar, ab, ap);
-  ar = block_sum_n(ar, sh);
-  ab = block_sum_n(ab, sh);
-  ap = block_sum_n(ap, sh);
-  const int nb = gridDim.x;
-  if (threadIdx.x == 0) {
-    a.part[blockIdx.x] = ar;
-    a.part[nb + blockIdx.x] = ab;
-    a.part[2 * nb + blockIdx.x] = ap;
-  }
-  if (!grid_sync(a.bar, a.status)) return false;
-  r2 = sum_partials(a.part, nb, sh);
-  b2 = sum_partials(a.part + nb, nb, sh);
-  ps = sum_partials(a.part + 2 * nb, nb, sh);
-  return true;
-}
-
 template <typename T, bool DFM>
 __global__ void __launch_bounds__(kPB, 2) k_poisson(PArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[kPB];
   __shared__ T sht[kPB];
-  const long long G = (long long)gridDim.x * blockDim.x;
-  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const Level<T> L0 = a.lv[0];  // descriptors by value: stores cannot alias them
-  const Dims d = L0.dims();
-  const long long N = d.N;
-  PDev *st = a.st;
-  const int have_prev = st->have_prev;
-
-  // initial guess, level-0 face coefficients, sum of q
-  double accq = 0.0;
-  for (long long i = gt; i < N; i += G) {
-    if constexpr (DFM) {
-      const DF p{a.phi_hi[i], a.phi_lo[i]};
-      if (have_prev) {
-        const DF g = df_sub(DF{2.f * p.hi, 2.f * p.lo}, DF{a.prev_hi[i], a.prev_lo[i]});
-        a.phi_hi[i] = g.hi;
-        a.phi_lo[i] = g.lo;
-      }
-      a.prev_hi[i] = p.hi;
-      a.prev_lo[i] = p.lo;
-    } else {
-      const double p = a.phi[i];
-      if (have_prev) a.phi[i] = 2.0 * p - a.prev[i];
-      a.prev[i] = p;
-    }
-    if (!L0.eps) {
-      int x, y, z;
-      coords(d, i, x, y, z);
-      const T e = a.eps[i];
-      L0.k[0][i] = T(0.5) * (e + a.eps[site(d, wrapp(x, d.nx), y, z)]);
-      L0.k[1][i] = T(0.5) * (e + a.eps[site(d, x, wrapp(y, d.ny), z)]);
-      L0.k[2][i] = T(0.5) * (e + a.eps[site(d, x, y, wrapp(z, d.nz))]);
-    }
-    accq += double(a.q[i]);
-  }
-  accq = block_sum_n(accq, sh);
-  if (threadIdx.x == 0) a.part[blockIdx.x] = accq;
-  if (!grid_sync(a.bar, a.status)) return;
-  const double qbar = sum_partials(a.part, gridDim.x, sh) / double(N);
-  const DF qbar_df = df_split(qbar);
-  // coarse face coefficients, level by level
-  for (int l = 1; l < a.nlev; ++l) {
-    const Level<T> F = a.lv[l - 1], C = a.lv[l];
-    const Dims f = F.dims(), c = C.dims();
-    for (long long I = gt; I < c.N; I += G) {
-      int X, Y, Z;
-      coords(c, I, X, Y, Z);
-      const int base[3] = {C.cf[0] ? 2 * X : X, C.cf[1] ? 2 * Y : Y, C.cf[2] ? 2 * Z : Z};
-      for (int ax = 0; ax < 3; ++ax) {
-        T acc = T(0);
-        int cnt = 0;
-        const int ra = C.cf[ax] ? 1 : 0;
-        const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
-        for (int t1 = 0; t1 <= C.cf[b1]; ++t1)
-          for (int t2 = 0; t2 <= C.cf[b2]; ++t2) {
-            int pp[3];
-            pp[ax] = base[ax] + ra;
-            pp[b1] = base[b1] + t1;
-            pp[b2] = base[b2] + t2;
-            const long long fi = site(f, pp[0], pp[1], pp[2]);
-            if (F.eps) {
-              int q[3] = {pp[0], pp[1], pp[2]};
-              q[ax] = q[ax] + 1 == (ax == 0 ? f.nx : ax == 1 ? f.ny : f.nz) ? 0 : q[ax] + 1;
-              acc += T(0.5) * (F.eps[fi] + F.eps[site(f, q[0], q[1], q[2])]);
-            } else {
-              acc += F.k[ax][fi];
-            }
-            ++cnt;
-          }
-        C.k[ax][I] = acc / T(cnt);
-      }
-    }
-    if (!grid_sync(a.bar, a.status)) return;
-  }
-  // residual test
-  double r2, b2, ps;
-  if (!residual_pass<T, DFM>(a, L0, qbar, qbar_df, sh, r2, b2, ps)) return;
-  const double tol = st->tol;
-  const int max_iter = st->max_iter;
-  const double bn = b2;
-  double rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
-  int it = 0;
-  // In the FP32 modes the level-0 residual is carried from cycle to cycle in
-  // FP32 (r <- r - A e); that estimate is accurate to about 1e-5 of the
-  // starting residual, so below kTrustTol the exact double-float residual
-  // re-anchors it before convergence is accepted.
-  bool exact = true;
-  const bool carry = DFM && tol >= kTrustTol;
-  double rr0 = rr;
-  for (;;) {
-  while (rr >= tol && it < max_iter) {
-    exact = !carry;
-    // V-cycle on the correction: levels above the tail, red-black smoothing
-    for (int l = 0; l < a.tail; ++l) {
-      const Level<T> Ll = a.lv[l];
-      const Level<T> Lc = a.lv[l + 1];
-      for (int s = 0; s < kNu; ++s) {
-        if (s == 0) {
-          // first red half sweep from x = 0 (neighbours are black and still unset)
-          const unsigned hx = unsigned(Ll.nx / 2);
-          for (long long t = gt; t < Ll.N / 2; t += G) {
-            const unsigned r = unsigned(t) / hx;
-            const int xh = int(unsigned(t) - r * hx);
-            const int z = int(r / unsigned(Ll.ny));
-            const int y = int(r - unsigned(z) * unsigned(Ll.ny));
-            const int x = 2 * xh + ((y + z) & 1);
-            const Dims dl = Ll.dims();
-            const long long i = site(dl, x, y, z);
-            const Faces<T> fc = faces(Ll, i, site(dl, wrapp(x, dl.nx), y, z), site(dl, wrapm(x, dl.nx), y, z),
-                                      site(dl, x, wrapp(y, dl.ny), z), site(dl, x, wrapm(y, dl.ny), z),
-                                      site(dl, x, y, wrapp(z, dl.nz)), site(dl, x, y, wrapm(z, dl.nz)));
-            const T diag = Ll.h[0] * (fc.xp + fc.xm) + Ll.h[1] * (fc.yp + fc.ym) + Ll.h[2] * (fc.zp + fc.zm);
-            Ll.x[i] = -Ll.b[i] / diag;
-          }
-        } else {
-          rb_range(Ll, 0, gt, G);
-        }
-        if (!grid_sync(a.bar, a.status)) return;
-        rb_range(Ll, 1, gt, G);
-        if (!grid_sync(a.bar, a.status)) return;
-      }
-      restrict_range(Ll, Lc, gt, G);
-      if (!grid_sync(a.bar, a.status)) return;
-    }
-    if (blockIdx.x == 0) tail_vcycle(a.lv, a.nlev, a.tail, smem_raw, sht);
-    if (!grid_sync(a.bar, a.status)) return;
-    for (int l = a.tail - 1; l >= 0; --l) {
-      const Level<T> Ll = a.lv[l];
-      const Level<T> Lc = a.lv[l + 1];
-      prolong_range(Ll, Lc, gt, G);
-      if (!grid_sync(a.bar, a.status)) return;
-      for (int s = 0; s < kNu; ++s) {
-        rb_range(Ll, 0, gt, G);
-        if (!grid_sync(a.bar, a.status)) return;
-        rb_range(Ll, 1, gt, G);
-        if (!grid_sync(a.bar, a.status)) return;
-      }
-    }
-    // phi += correction; the residual follows the correction
-    if (carry) {
-      // FP32 modes: r <- r - A e on the FP32 level-0 residual (its rounding error is
-      // relative to |A e| ~ |r|), phi += e in double-float; the double-float residual
-      // of the first pass fixes the starting point of each solve
-      double ar = 0.0, ap = 0.0;
-      for (long long i = gt; i < N; i += G) {
-        int x, y, z;
-        coords(d, i, x, y, z);
-        const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
-        const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
-        const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
-        const T *e = L0.x;
-        const T ei = e[i];
-        const Faces<T> fc = faces(L0, i, ixp, ixm, iyp, iym, izp, izm);
-        const T Ae = fc.xp * (e[ixp] - ei) + fc.xm * (e[ixm] - ei) + fc.yp * (e[iyp] - ei) + fc.ym * (e[iym] - ei) +
-                     fc.zp * (e[izp] - ei) + fc.zm * (e[izm] - ei);
-        const T r = L0.b[i] - Ae;
-        L0.b[i] = r;
-        ar += double(r * r);
-        const DF s = df_add(DF{a.phi_hi[i], a.phi_lo[i]}, DF{float(ei), 0.f});
-        a.phi_hi[i] = s.hi;
-        a.phi_lo[i] = s.lo;
-        ap += double(s.hi);
-      }
-      ar = block_sum_n(ar, sh);
-      ap = block_sum_n(ap, sh);
-      const int nb = gridDim.x;
-      if (threadIdx.x == 0) {
-        a.part[blockIdx.x] = ar;
-        a.part[2 * nb + blockIdx.x] = ap;
-      }
-      if (!grid_sync(a.bar, a.status)) return;
-      r2 = sum_partials(a.part, nb, sh);
-      ps = sum_partials(a.part + 2 * nb, nb, sh);
-    } else {
-      for (long long i = gt; i < N; i += G) {
-        if constexpr (DFM) {
-          const DF s = df_add(DF{a.phi_hi[i], a.phi_lo[i]}, DF{float(L0.x[i]), 0.f});
-          a.phi_hi[i] = s.hi;
-          a.phi_lo[i] = s.lo;
-        } else {
-          a.phi[i] += double(L0.x[i]);
-        }
-      }
-      if (!grid_sync(a.bar, a.status)) return;
-      if (!residual_pass<T, DFM>(a, L0, qbar, qbar_df, sh, r2, b2, ps)) return;
-    }
-    rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
-    ++it;
-  }
-  if (exact || rr + kEstErr * rr0 < tol) break;
-  if (!residual_pass<T, DFM>(a, L0, qbar, qbar_df, sh, r2, b2, ps)) return;
-  rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
-  rr0 = rr;
-  exact = true;
-  if (rr < tol || it >= max_iter) break;
-  }
-  const bool zero = bn == 0.0;
-  const double mean_phi = ps / double(N);
-  const DF mean_df = df_split(mean_phi);
-  for (long long i = gt; i < N; i += G) {
-    if constexpr (DFM) {
-      DF v{0.f, 0.f};
-      if (!zero) v = df_sub(DF{a.phi_hi[i], a.phi_lo[i]}, mean_df);
-      a.phi_hi[i] = v.hi;
-      a.phi_lo[i] = v.lo;
-    } else {
-      a.phi[i] = zero ? 0.0 : a.phi[i] - mean_phi;
-    }
-  }
-  if (gt == 0) {
-    st->mean_q = qbar;
-    st->mean_phi = mean_phi;
-    st->bnorm2 = bn;
-    st->rnorm2 = r2;
-    st->relres = rr;
-    st->iters = it;
-    st->total_iters += it;
-    const int fail = rr >= tol;
-    st->notconv = fail;
-    st->cond = 0;
-    st->zero = zero;
-    st->have_prev = 1;
-    if (fail) atomicOr(a.status, ST_POISSON);
-  }
+  poisson_body<T, DFM>(a, GridTeam{a.bar, a.status}, smem_raw, sh, sht);
 }
 
 // ---------------------------------------------------------------- host
@@ -1139,7 +430,7 @@ template <typename T, bool DFM> static void persistent_setup(Poisson *p, const C
   tl.n = (int)L.size();
   for (size_t l = 0; l < L.size(); ++l) tl.L[l] = L[l];
   const size_t smem = tail_bytes(tl, (int)ts);
-  if (cudaFuncSetAttribute(k_poisson<T, DFM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (!raise_smem_limit((const void *)k_poisson<T, DFM>, smem))
     return;
   int dev = 0, nsm = 0, coop = 0, per = 0;
   cudaGetDevice(&dev);
@@ -1160,7 +451,7 @@ template <typename T, bool DFM> static void persistent_setup(Poisson *p, const C
   p->ptail_smem = smem;
 }
 
-template <typename T, bool DFM> static int persistent_launch(Poisson *p, Ctx &c, cudaStream_t s) {
+template <typename T, bool DFM> static PArgs<T> fill_args(Poisson *p, const Ctx &c) {
   auto &L = levels<T>(p);
   PArgs<T> a{};
   a.lv = (const Level<T> *)p->dlevels;
@@ -1185,6 +476,11 @@ template <typename T, bool DFM> static int persistent_launch(Poisson *p, Ctx &c,
   a.status = c.status;
   a.part = p->part;
   a.bar = p->bar;
+  return a;
+}
+
+template <typename T, bool DFM> static int persistent_launch(Poisson *p, Ctx &c, cudaStream_t s) {
+  const PArgs<T> a = fill_args<T, DFM>(p, c);
   if (cudaMemsetAsync(p->bar, 0, sizeof(Bar), s) != cudaSuccess) return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p->pgrid);
@@ -1416,6 +712,56 @@ int poisson_solve(Poisson *p, Ctx &c, double *relres) {
 int poisson_capture(Poisson *p, Ctx &c, cudaGraphConditionalHandle handle) {
   double rr = 0;
   return p->fp64 ? enqueue<double>(p, c, handle, true, &rr) : enqueue<float>(p, c, handle, true, &rr);
+}
+
+// Level table in device memory for a solve by one team (built here when the
+// cooperative solve was not set up); -1 when a level above the tail cannot be
+// coloured red-black.
+template <typename T, bool DFM> static long long team_setup(Poisson *p, const Ctx &c) {
+  auto &L = levels<T>(p);
+  const size_t ts = tail_start(L);
+  for (size_t l = 0; l < ts; ++l)
+    if (!L[l].rb) return -1;
+  Tail<T> tl;
+  tl.n = (int)L.size();
+  for (size_t l = 0; l < L.size(); ++l) tl.L[l] = L[l];
+  const size_t smem = tail_bytes(tl, (int)ts);
+  if (!p->dlevels) {
+    std::vector<Level<T>> tab(L.begin(), L.end());
+    if (ts > 0) tab[0].eps = (const T *)c.eps;
+    Level<T> *d = alloc<Level<T>>(p, (long long)tab.size());
+    if (!d || cudaMemcpy(d, tab.data(), tab.size() * sizeof(Level<T>), cudaMemcpyHostToDevice) != cudaSuccess)
+      return -1;
+    p->dlevels = d;
+  }
+  return (long long)smem;
+}
+
+long long poisson_team_args(Poisson *p, const Ctx &c, void *out, size_t out_bytes) {
+  if (p->fp64) {
+    if (out_bytes != sizeof(PArgs<double>)) return -1;
+    const long long smem = team_setup<double, false>(p, c);
+    if (smem < 0) return -1;
+    const PArgs<double> a = fill_args<double, false>(p, c);
+    std::memcpy(out, &a, sizeof(a));
+    return smem;
+  }
+  if (out_bytes != sizeof(PArgs<float>)) return -1;
+  const long long smem = team_setup<float, true>(p, c);
+  if (smem < 0) return -1;
+  const PArgs<float> a = fill_args<float, true>(p, c);
+  std::memcpy(out, &a, sizeof(a));
+  return smem;
+}
+
+void poisson_state_buffers(Poisson *p, const Ctx &c, std::vector<std::pair<void *, size_t>> &out) {
+  if (p->fp64) {
+    out.emplace_back(p->phi_prev, 8 * (size_t)c.d.N);
+  } else {
+    out.emplace_back(p->prev_hi, 4 * (size_t)c.d.N);
+    out.emplace_back(p->prev_lo, 4 * (size_t)c.d.N);
+  }
+  out.emplace_back(p->dev, sizeof(PDev));
 }
 
 int poisson_read(Poisson *p, cudaStream_t s, PoissonStats *out) {

@@ -67,15 +67,22 @@ __device__ __forceinline__ T permittivity(const StepK<T> &k, T ra, T rb, T ps) {
 }
 
 // ---------------------------------------------------------------- k_macro
-template <typename S, typename T, int NC>
-__global__ void __launch_bounds__(256) k_macro(StepK<T> k, const S *__restrict__ f, T *__restrict__ rho,
-                                               T *__restrict__ Jout, T *__restrict__ psi, T *__restrict__ eps,
-                                               T *__restrict__ q, const T *__restrict__ n,
-                                               const T *__restrict__ qc, const T *__restrict__ psi_s,
-                                               const uint8_t *__restrict__ solid) {
+// RO: the populations are read-only for the whole launch (separate kernels),
+// so they may go through the non-coherent read path; a kernel that also
+// writes them in an earlier phase passes false.
+template <bool RO, typename S, typename T>
+__device__ __forceinline__ T sload(const S *p, size_t i, T shift) {
+  if constexpr (RO) return Store<S, T>::ld(p, i, shift);
+  else return Store<S, T>::ldc(p, i, shift);
+}
+
+template <typename S, typename T, int NC, bool RO>
+__device__ __forceinline__ void macro_site(const StepK<T> &k, const S *__restrict__ f, T *__restrict__ rho,
+                                           T *__restrict__ Jout, T *__restrict__ psi, T *__restrict__ eps,
+                                           T *__restrict__ q, const T *__restrict__ n, const T *__restrict__ qc,
+                                           const T *__restrict__ psi_s, const uint8_t *__restrict__ solid,
+                                           const long long i) {
   const long long N = k.d.N;
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= N) return;
   T r[2] = {T(0), T(0)};
   T J[3] = {T(0), T(0), T(0)};
   const bool sol = k.solids && solid[i];
@@ -86,7 +93,7 @@ __global__ void __launch_bounds__(256) k_macro(StepK<T> k, const S *__restrict__
       T acc = T(0);
 #pragma unroll
       for (int qd = 0; qd < 19; ++qd) {
-        fl[s][qd] = Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]);
+        fl[s][qd] = sload<RO, S, T>(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]);
         acc += fl[s][qd];
       }
       r[s] = acc;
@@ -114,6 +121,17 @@ __global__ void __launch_bounds__(256) k_macro(StepK<T> k, const S *__restrict__
   T qq = k.solids ? qc[i] : T(0);
   if (k.nions) qq += n[i] - n[N + i];
   q[i] = qq;
+}
+
+template <typename S, typename T, int NC>
+__global__ void __launch_bounds__(256) k_macro(StepK<T> k, const S *__restrict__ f, T *__restrict__ rho,
+                                               T *__restrict__ Jout, T *__restrict__ psi, T *__restrict__ eps,
+                                               T *__restrict__ q, const T *__restrict__ n,
+                                               const T *__restrict__ qc, const T *__restrict__ psi_s,
+                                               const uint8_t *__restrict__ solid) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= k.d.N) return;
+  macro_site<S, T, NC, true>(k, f, rho, Jout, psi, eps, q, n, qc, psi_s, solid, i);
 }
 
 // ---------------------------------------------------------------- k_virtual
@@ -174,17 +192,16 @@ __global__ void k_virtual(StepK<T> k, T *__restrict__ rho, T *__restrict__ psi, 
 // loaded, relaxed and pushed.  Keeping the populations out of the force
 // phase holds the register footprint low enough for several resident blocks
 // per SM.  Site indices are 32-bit (boxes below 2^31 sites).
-template <typename S, typename T, int NC, bool SOL, bool IONS>
-__global__ void __launch_bounds__(256, 3)
-    k_collide(StepK<T> k, const S *__restrict__ f, S *__restrict__ fn, const T *__restrict__ rhoF,
-              const T *__restrict__ JF, const T *__restrict__ psiF, const T *__restrict__ eps,
-              const T *__restrict__ phi, const T *__restrict__ n, const T *__restrict__ psi_f,
-              const uint8_t *__restrict__ solid, const int *__restrict__ owner, const double *__restrict__ cv,
-              T *__restrict__ u_out, T *__restrict__ flux_out) {
+template <typename S, typename T, int NC, bool SOL, bool IONS, bool RO>
+__device__ __forceinline__ void collide_site(const StepK<T> &k, const S *__restrict__ f, S *__restrict__ fn,
+                                             const T *__restrict__ rhoF, const T *__restrict__ JF,
+                                             const T *__restrict__ psiF, const T *__restrict__ eps,
+                                             const T *__restrict__ phi, const T *__restrict__ n,
+                                             const T *__restrict__ psi_f, const uint8_t *__restrict__ solid,
+                                             const int *__restrict__ owner, const double *__restrict__ cv,
+                                             T *__restrict__ u_out, T *__restrict__ flux_out, const int i) {
   const int nx = k.d.nx, ny = k.d.ny, nz = k.d.nz;
   const int N = int(k.d.N);
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= N) return;
   if (SOL && solid[i]) {
     // a node covered by a moving colloid must not keep the face fluxes and
     // velocity of the step in which it was fluid
@@ -395,7 +412,7 @@ __global__ void __launch_bounds__(256, 3)
     const T sh = k.shift[s];
     T fl[19];
 #pragma unroll
-    for (int qd = 0; qd < 19; ++qd) fl[qd] = Store<S, T>::ld(fs, (size_t)qd * N + i, wq<T>(qd) * sh);
+    for (int qd = 0; qd < 19; ++qd) fl[qd] = sload<RO, S, T>(fs, (size_t)qd * N + i, wq<T>(qd) * sh);
     const T usq = ue[s][0] * ue[s][0] + ue[s][1] * ue[s][1] + ue[s][2] * ue[s][2];
 #pragma unroll
     for (int qd = 0; qd < 19; ++qd) {
@@ -420,15 +437,26 @@ __global__ void __launch_bounds__(256, 3)
   }
 }
 
+template <typename S, typename T, int NC, bool SOL, bool IONS>
+__global__ void __launch_bounds__(256, 3)
+    k_collide(StepK<T> k, const S *__restrict__ f, S *__restrict__ fn, const T *__restrict__ rhoF,
+              const T *__restrict__ JF, const T *__restrict__ psiF, const T *__restrict__ eps,
+              const T *__restrict__ phi, const T *__restrict__ n, const T *__restrict__ psi_f,
+              const uint8_t *__restrict__ solid, const int *__restrict__ owner, const double *__restrict__ cv,
+              T *__restrict__ u_out, T *__restrict__ flux_out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= int(k.d.N)) return;
+  collide_site<S, T, NC, SOL, IONS, true>(k, f, fn, rhoF, JF, psiF, eps, phi, n, psi_f, solid, owner, cv, u_out,
+                                          flux_out, i);
+}
+
 // ---------------------------------------------------------------- k_np
 template <typename T, bool SOL>
-__global__ void __launch_bounds__(256) k_np(StepK<T> k, const T *__restrict__ n, T *__restrict__ nn,
-                                            const T *__restrict__ flux, const T *__restrict__ u,
-                                            const uint8_t *__restrict__ solid) {
+__device__ __forceinline__ void np_site(const StepK<T> &k, const T *__restrict__ n, T *__restrict__ nn,
+                                        const T *__restrict__ flux, const T *__restrict__ u,
+                                        const uint8_t *__restrict__ solid, const long long i) {
   const Dims d = k.d;
   const long long N = d.N;
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= N) return;
   if (SOL && solid[i]) {
     nn[i] = T(0);
     nn[N + i] = T(0);
@@ -473,6 +501,15 @@ __global__ void __launch_bounds__(256) k_np(StepK<T> k, const T *__restrict__ n,
     }
     nn[s * N + i] = ((ni + div) - out) + in;
   }
+}
+
+template <typename T, bool SOL>
+__global__ void __launch_bounds__(256) k_np(StepK<T> k, const T *__restrict__ n, T *__restrict__ nn,
+                                            const T *__restrict__ flux, const T *__restrict__ u,
+                                            const uint8_t *__restrict__ solid) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= k.d.N) return;
+  np_site<T, SOL>(k, n, nn, flux, u, solid, i);
 }
 
 // ---------------------------------------------------------------- init / read-out

@@ -97,6 +97,12 @@ def _load():
     lib.lbeh_profile_read.argtypes = [H, C.POINTER(lbeh_profile)]
     lib.lbeh_observables_noalloc.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                              C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(lbeh_obs), C.c_void_p]
+    lib.lbeh_create_batch.argtypes = [C.POINTER(lbeh_params), C.c_int, C.POINTER(H)]
+    lib.lbeh_batch_box.argtypes = [H, C.c_int, C.POINTER(H)]
+    lib.lbeh_batch_step_sequential.argtypes = [H, C.c_int]
+    lib.lbeh_batch_tune.argtypes = [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    lib.lbeh_batch_set_shape.argtypes = [H, C.c_int]
+    lib.lbeh_batch_shape.argtypes = [H]
     lib.lbeh_destroy.argtypes = [H]
     lib.lbeh_destroy.restype = None
     lib.lbeh_last_error.argtypes = [H]
@@ -104,7 +110,9 @@ def _load():
     lib.lbeh_status_string.argtypes = [C.c_int]
     lib.lbeh_status_string.restype = C.c_char_p
     for name in ("lbeh_create", "lbeh_set_fields", "lbeh_get_fields", "lbeh_step", "lbeh_observables",
-                 "lbeh_get_aux", "lbeh_profile_enable", "lbeh_profile_read", "lbeh_observables_noalloc"):
+                 "lbeh_get_aux", "lbeh_profile_enable", "lbeh_profile_read", "lbeh_observables_noalloc",
+                 "lbeh_create_batch", "lbeh_batch_box", "lbeh_batch_step_sequential", "lbeh_batch_tune",
+                 "lbeh_batch_set_shape", "lbeh_batch_shape"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -189,6 +197,41 @@ def lbeh_observables_noalloc(nx, ny, nz, ncomp, nions, dtype, f_ptr, n_ptr=None,
     return o
 
 
+def lbeh_create_batch(params_list) -> C.c_void_p:
+    arr = (lbeh_params * len(params_list))(*params_list)
+    h = C.c_void_p()
+    _check(_lib.lbeh_create_batch(arr, len(params_list), C.byref(h)), "lbeh_create_batch")
+    return h
+
+
+def lbeh_batch_box(h, b: int) -> C.c_void_p:
+    box = C.c_void_p()
+    _check(_lib.lbeh_batch_box(h, int(b), C.byref(box)), "lbeh_batch_box")
+    return box
+
+
+def lbeh_batch_step_sequential(h, nsteps: int) -> int:
+    rc = _lib.lbeh_batch_step_sequential(h, int(nsteps))
+    if rc not in (LBEH_OK, LBEH_ERR_POISSON_NOT_CONVERGED):
+        raise LbehError(rc, "lbeh_batch_step_sequential [%s]" % lbeh_last_error(h))
+    return rc
+
+
+def lbeh_batch_tune(h, probe_steps: int):
+    cpb = C.c_int()
+    ms = C.c_double()
+    _check(_lib.lbeh_batch_tune(h, int(probe_steps), C.byref(cpb), C.byref(ms)), "lbeh_batch_tune")
+    return cpb.value, ms.value
+
+
+def lbeh_batch_set_shape(h, cluster_blocks: int) -> int:
+    return _check(_lib.lbeh_batch_set_shape(h, int(cluster_blocks)), "lbeh_batch_set_shape")
+
+
+def lbeh_batch_shape(h) -> int:
+    return int(_lib.lbeh_batch_shape(h))
+
+
 def lbeh_destroy(h) -> None:
     _lib.lbeh_destroy(h)
 
@@ -239,10 +282,12 @@ class System:
     Field arguments are numpy arrays (host) or torch CUDA tensors (device) of
     float64 or float32, shaped like the C-ABI layout."""
 
-    def __init__(self, params, stream: int = 0):
+    def __init__(self, params, stream: int = 0, handle=None):
         self.params = params
         self.cparams = make_params(params, stream)
-        self.h = lbeh_create(self.cparams)
+        # handle: a box of a batch (owned by the batch, not released here)
+        self.owned = handle is None
+        self.h = lbeh_create(self.cparams) if handle is None else handle
         self.N = int(params.nx) * int(params.ny) * int(params.nz)
         self.shape = (int(params.nz), int(params.ny), int(params.nx))
         self.ncomp = int(params.ncomp)
@@ -251,7 +296,8 @@ class System:
 
     def close(self):
         if self.h:
-            lbeh_destroy(self.h)
+            if self.owned:
+                lbeh_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -371,3 +417,41 @@ class System:
         else:
             out = np.zeros(shp)
         return lbeh_get_aux(self.h, which, out)
+
+
+class Batch:
+    """Independent systems advanced together by one launch per step call
+    (marshalling only); box b is a System view owned by the batch."""
+
+    def __init__(self, params_list, stream: int = 0):
+        self.params = list(params_list)
+        self.h = lbeh_create_batch([make_params(p, stream) for p in self.params])
+        self.boxes = [System(p, stream, handle=lbeh_batch_box(self.h, b)) for b, p in enumerate(self.params)]
+
+    def step(self, nsteps: int = 1) -> int:
+        return lbeh_step(self.h, nsteps)
+
+    def step_sequential(self, nsteps: int = 1) -> int:
+        return lbeh_batch_step_sequential(self.h, nsteps)
+
+    def tune(self, probe_steps: int = 4):
+        return lbeh_batch_tune(self.h, probe_steps)
+
+    def set_shape(self, cluster_blocks: int):
+        lbeh_batch_set_shape(self.h, cluster_blocks)
+
+    def shape(self) -> int:
+        return lbeh_batch_shape(self.h)
+
+    def close(self):
+        if self.h:
+            for b in self.boxes:
+                b.h = None
+            lbeh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -15,7 +15,11 @@ def oracle_for(w, phi=None):
 
 
 def gpu_for(w, lbeh, stream=0):
-    s = lbeh.System(w.params, stream)
+    return load(lbeh.System(w.params, stream), w)
+
+
+def load(s, w):
+    """Load workload w into the System (or box view) s."""
     nc = len(w.colloid_r)
     s.set_fields(rho=list(w.rho), n=list(w.n) if w.n is not None else None, u=w.u,
                  colloid_x=w.colloid_x if nc else None, colloid_v=w.colloid_v if nc else None,

@@ -27,3 +27,12 @@ def pytest_collection_modifyitems(config, items):
     for item in items:
         if "gpu" in item.keywords:
             item.add_marker(skip)
+
+
+@pytest.fixture(scope="module")
+def lbeh():
+    """The CUDA library's binding (built in-tree on first use)."""
+    import paper_1712_08494_gb300 as pkg
+    pkg.build()
+    from paper_1712_08494_gb300 import lbeh as L
+    return L
