@@ -206,6 +206,52 @@ int lbeh_observables_noalloc(int nx, int ny, int nz, int ncomp, int nions, int d
                              const void *n, const uint8_t *solid, const double *qc, lbeh_obs *out,
                              void *stream);
 
+/* Gradients through nsteps coupled steps by the discrete adjoint.
+ *
+ * The objective is J = d_deformation * D(t_end) + sum f_bar . f(t_end)
+ * + sum n_bar . n(t_end), with D the drop deformation of lbeh_observables
+ * (second moments of w = max(c, 0), c = (rho_b - rho_a)/(rho_a + rho_b)).
+ * lbeh_step_adjoint advances the handle by nsteps exactly as lbeh_step does,
+ * keeping a checkpoint of (f, n) every ckpt_every steps and the potential of
+ * every step, then sweeps backwards: each segment is recomputed from its
+ * checkpoint, and each step is reversed by hand-written adjoint kernels (the
+ * transposes of collision, streaming, Shan-Chen, Kelvin and friction forces,
+ * ion face fluxes and upwind advection) plus one adjoint Poisson solve with
+ * the same multigrid solver (the operator is symmetric).
+ *
+ * Supported: two components, nions 0 or 2 without solvation (dmu = 0), no
+ * colloids, prec LBEH_FP64 or LBEH_FP32 (UNSUPPORTED otherwise).  Outputs:
+ * dJ/dE_ext, dJ/dG, dJ/dQ = sum n0_bar . dn0_dQ for a caller-given
+ * derivative of the initial ions with respect to a charge Q (for instance the
+ * drop charge placement of a synthetic input), and optionally the adjoint
+ * state at the start (f0_bar, n0_bar).  FP64 arrays; host or device per
+ * on_device.  Synchronises.  Afterwards the handle is in the state lbeh_step
+ * would leave (fields of the last step included).  A Poisson solve of either
+ * sweep that misses its tolerance returns LBEH_ERR_POISSON_NOT_CONVERGED with
+ * the gradients filled in. */
+typedef struct lbeh_obs_seed {
+  double d_deformation; /* dJ/dD of the final state */
+  const double *f_bar;  /* optional [2][19][N]: dJ/df(t_end) */
+  const double *n_bar;  /* optional [2][N]: dJ/dn(t_end) */
+  int on_device;        /* f_bar and n_bar are device pointers */
+} lbeh_obs_seed;
+
+typedef struct lbeh_grads {
+  double deformation;        /* D(t_end) */
+  double dE_ext[3];          /* dJ/dE_ext */
+  double dG;                 /* dJ/dG (Shan-Chen coupling) */
+  double dQ;                 /* sum n0_bar . dn0_dQ (0 when dn0_dQ is NULL) */
+  const double *dn0_dQ;      /* input, optional [2][N] */
+  double *f0_bar;            /* output, optional [2][19][N]: dJ/df(t_start) */
+  double *n0_bar;            /* output, optional [2][N]: dJ/dn(t_start) */
+  int on_device;             /* dn0_dQ, f0_bar and n0_bar are device pointers */
+  double forward_ms;         /* device time of the forward sweep */
+  double adjoint_ms;         /* device time of the reverse sweep (recompute included) */
+  long long adjoint_poisson_cycles; /* multigrid cycles of the adjoint Poisson solves */
+} lbeh_grads;
+
+int lbeh_step_adjoint(lbeh_handle *h, int nsteps, int ckpt_every, const lbeh_obs_seed *seed, lbeh_grads *out);
+
 /* Batches of independent systems (the model of Sec. II on each, no coupling
  * between them), for parameter sweeps over many small boxes of uneven size.
  *

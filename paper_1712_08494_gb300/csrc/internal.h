@@ -163,6 +163,30 @@ int batch_box_status(const Batch *b, int box);  // status word of a box read by 
 // each) and keeps the fastest.
 int batch_tune(Batch *b, int probe_steps, int *best_blocks, double *best_ms_per_step);
 
+// Discrete adjoint of the coupled step (adjoint_<prec>.cu): kernel passes of
+// one reversed step on plain device arrays in the compute type.
+struct AdjArgs {
+  const void *f, *n;                                     // forward state at t
+  const void *rho, *J, *psi, *eps, *phi, *u, *flux;      // forward fields of step t
+  const void *fbo, *nbo;                                 // adjoint state at t+1
+  void *fbn, *nbn;                                       // adjoint state at t
+  void *rb, *Jb, *Felb, *KC, *Sb, *psib, *epsb, *Fb, *Efb, *Eb, *qadj;  // work arrays
+  const void *lam;                                       // adjoint potential (compute type)
+};
+constexpr int kAdjBlocks = 1024;  // fixed grid of the passes with parameter sums
+constexpr int kAdjPar = 4;        // dJ/dE_x, dJ/dE_y, dJ/dE_z, dJ/dG per block
+struct AdjOps {
+  // passes before the adjoint Poisson solve (its right-hand side lands in qadj)
+  void (*before_solve)(const Ctx &, const AdjArgs &, double *part) = nullptr;
+  // passes after it (lam holds the solution); completes fbn and nbn
+  void (*after_solve)(const Ctx &, const AdjArgs &, double *part) = nullptr;
+  // adds scale * dD/df of the drop deformation to fb; mom = {X, Z, sqrt(Mxx), sqrt(Mzz)}
+  void (*seed)(const Ctx &, const void *f, void *fb, const double mom[4], double scale) = nullptr;
+  size_t elem = 0;
+};
+AdjOps adj_ops_f64();
+AdjOps adj_ops_f32();
+
 // Deterministic FP64 reductions (reduce.cu).
 void reduce_partials_final(const double *partials, int nblocks, int len, double *out, cudaStream_t s);
 double dot_f64(const double *a, const double *b, long long n, double *scratch, cudaStream_t s);

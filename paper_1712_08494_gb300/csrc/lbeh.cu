@@ -53,6 +53,7 @@ struct lbeh_handle {
   std::vector<lbeh_handle *> boxes;
   lbeh_handle *parent = nullptr;
   bool stats_stale = false;  // Poisson statistics not read back since a batched step
+  Poisson *adj_pois = nullptr;  // solver of the adjoint Poisson problems (created on first use)
 };
 
 std::atomic<long long> lbeh::g_launches{0};
@@ -69,6 +70,10 @@ __global__ void k_mask_fluid(T *__restrict__ a, const uint8_t *__restrict__ soli
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= N || !solid[i]) return;
   for (int s = 0; s < ncomp; ++s) a[s * N + i] = T(0);
+}
+
+__global__ void k_add(double *__restrict__ acc, const double *__restrict__ v, int n) {
+  if (threadIdx.x < n) acc[threadIdx.x] += v[threadIdx.x];
 }
 
 inline bool cuda_ok(cudaError_t e) { return e == cudaSuccess; }
@@ -581,6 +586,7 @@ static void destroy_handle(lbeh_handle *h) {
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
   poisson_destroy(h->pois);
+  poisson_destroy(h->adj_pois);
   for (void *a : h->allocs) cudaFree(a);
   delete h;
 }
@@ -764,17 +770,23 @@ int lbeh_step(lbeh_handle *h, int nsteps) {
 
 const char *lbeh_last_error(lbeh_handle *h) { return h ? h->last_error : "no handle"; }
 
+// Fixed-order FP64 sums of the observables (layout of k_obs) on the host.
+static int obs_sums(lbeh_handle *h, double v[kObsLen]) {
+  Ctx &c = h->c;
+  h->ops.obs_partials(c, c.red, kRedBlocks);
+  double *res = c.red + (size_t)kRedBlocks * kObsLen;
+  reduce_partials_final(c.red, kRedBlocks, kObsLen, res, c.s);
+  cudaMemcpyAsync(v, res, sizeof(double) * kObsLen, cudaMemcpyDeviceToHost, c.s);
+  return cudaStreamSynchronize(c.s) == cudaSuccess ? LBEH_OK : LBEH_ERR_CUDA;
+}
+
 int lbeh_observables(lbeh_handle *h, lbeh_obs *out) {
   if (!h || !out) return LBEH_ERR_INVALID_ARG;
   if (h->batch) return LBEH_ERR_INVALID_ARG;
   Ctx &c = h->c;
   std::memset(out, 0, sizeof(*out));
-  h->ops.obs_partials(c, c.red, kRedBlocks);
-  double *res = c.red + (size_t)kRedBlocks * kObsLen;
-  reduce_partials_final(c.red, kRedBlocks, kObsLen, res, c.s);
   double v[kObsLen];
-  cudaMemcpyAsync(v, res, sizeof(v), cudaMemcpyDeviceToHost, c.s);
-  if (cudaStreamSynchronize(c.s) != cudaSuccess) return LBEH_ERR_CUDA;
+  if (obs_sums(h, v) != LBEH_OK) return LBEH_ERR_CUDA;
   for (int m = 0; m < kObsLen; ++m)
     if (!std::isfinite(v[m])) h->status = LBEH_ERR_NONFINITE;
   out->mass[0] = v[0];
@@ -811,6 +823,267 @@ int lbeh_observables(lbeh_handle *h, lbeh_obs *out) {
   out->status = h->status;
   out->steps = h->steps;
   return LBEH_OK;
+}
+
+// ---------------------------------------------------------------- adjoint
+namespace {
+struct DevArena {
+  std::vector<void *> blocks;
+  bool ok = true;
+  void *get(size_t bytes) {
+    void *p = nullptr;
+    if (bytes == 0) return nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+      ok = false;
+      cudaGetLastError();
+      return nullptr;
+    }
+    blocks.push_back(p);
+    return p;
+  }
+  ~DevArena() {
+    for (void *p : blocks) cudaFree(p);
+  }
+};
+}  // namespace
+
+int lbeh_step_adjoint(lbeh_handle *h, int nsteps, int ckpt_every, const lbeh_obs_seed *seed, lbeh_grads *out) {
+  if (!h || h->batch || !seed || !out || nsteps < 1 || ckpt_every < 1 || !h->loaded) return LBEH_ERR_INVALID_ARG;
+  Ctx &c = h->c;
+  if (c.ncomp != 2 || c.ncoll_max > 0 || c.solvation || (c.prec != LBEH_FP64 && c.prec != LBEH_FP32))
+    return LBEH_ERR_UNSUPPORTED;
+  const AdjOps A = c.prec == LBEH_FP64 ? adj_ops_f64() : adj_ops_f32();
+  const size_t e = A.elem;
+  const long long N = c.d.N;
+  const size_t popB = e * 38 * N, ionB = c.nions ? e * 2 * N : 0, phiB = e * N, stB = popB + ionB;
+  const int K = std::min(ckpt_every, nsteps);
+  const int nseg = (nsteps + K - 1) / K;
+  const double *dn_user = out->dn0_dQ;
+  double *f0_user = out->f0_bar, *n0_user = out->n0_bar;
+  const int out_dev = out->on_device;
+
+  DevArena M;
+  char *ck = (char *)M.get(nseg * stB);
+  char *phis = (char *)M.get((size_t)nsteps * phiB);
+  char *seg = (char *)M.get((size_t)(K + 1) * stB);
+  void *fb[2] = {M.get(popB), M.get(popB)};
+  void *nbf[2] = {M.get(ionB), M.get(ionB)};
+  AdjArgs a{};
+  void *rb = M.get(e * 2 * N), *Jb = M.get(e * 3 * N), *Felb = M.get(e * 3 * N), *KC = M.get(e * 3 * N);
+  void *Sb = M.get(e * 6 * N), *psib = M.get(e * 2 * N), *epsb = M.get(e * N), *Eb = M.get(e * 3 * N);
+  void *qadj = M.get(e * N);
+  void *Fb = M.get(c.nions ? e * 6 * N : 0), *Efb = M.get(c.nions ? e * 3 * N : 0);
+  void *lam = M.get(c.prec == LBEH_FP64 ? 8 * N : 4 * N), *lam_lo = c.prec == LBEH_FP64 ? nullptr : M.get(4 * N);
+  double *part = (double *)M.get(8 * (size_t)kAdjBlocks * kAdjPar);
+  double *acc = (double *)M.get(8 * 16);
+  int *astatus = (int *)M.get(sizeof(int));  // status word of the adjoint solves
+  // last-step fields of the forward sweep (the reverse sweep reuses their buffers)
+  void *keep_rho = M.get(e * 2 * N), *keep_eps = M.get(e * N), *keep_q = M.get(e * N), *keep_u = M.get(e * 3 * N);
+  if (!M.ok) return LBEH_ERR_OOM;
+  cudaMemsetAsync(astatus, 0, sizeof(int), c.s);
+
+  // adjoint Poisson problem: same permittivity, right-hand side -(qadj - mean), no applied field
+  Ctx ca = c;
+  ca.q = qadj;
+  ca.status = astatus;
+  ca.Eext[0] = ca.Eext[1] = ca.Eext[2] = 0.0;
+  if (c.prec == LBEH_FP64) {
+    ca.phi = (double *)lam;
+    ca.phit = lam;
+  } else {
+    ca.phit = lam;
+    ca.phi_lo = (float *)lam_lo;
+  }
+  if (c.has_field) {
+    if (!h->adj_pois) {
+      h->adj_pois = poisson_create(ca, c.prec == LBEH_FP64);
+      if (!h->adj_pois) return LBEH_ERR_OOM;
+    }
+    if (poisson_configure(h->adj_pois, h->p.poisson_tol, h->p.poisson_max_iter, c.s) != 0 ||
+        poisson_reset(h->adj_pois, c.s) != 0)
+      return cuda_fail(h, "adjoint Poisson setup");
+  }
+  cudaMemsetAsync(lam, 0, c.prec == LBEH_FP64 ? 8 * N : 4 * N, c.s);
+  if (lam_lo) cudaMemsetAsync(lam_lo, 0, 4 * N, c.s);
+
+  cudaEvent_t ev[3];
+  for (auto &x : ev) cudaEventCreate(&x);
+  auto finish = [&](int rc) {
+    cudaStreamSynchronize(c.s);
+    for (auto &x : ev) cudaEventDestroy(x);
+    return rc;
+  };
+
+  // forward sweep: checkpoints of (f, n) every K steps, the potential of every step
+  cudaEventRecord(ev[0], c.s);
+  int worst = LBEH_OK;
+  for (int t = 0; t < nsteps; ++t) {
+    if (t % K == 0) {
+      char *dst = ck + (size_t)(t / K) * stB;
+      cudaMemcpyAsync(dst, c.f[c.cur], popB, cudaMemcpyDeviceToDevice, c.s);
+      if (ionB) cudaMemcpyAsync(dst + popB, c.n[c.ncur], ionB, cudaMemcpyDeviceToDevice, c.s);
+    }
+    const int rc = lbeh_step(h, 1);
+    if (rc != LBEH_OK && rc != LBEH_ERR_POISSON_NOT_CONVERGED) return finish(rc);
+    if (rc != LBEH_OK) worst = rc;
+    cudaMemcpyAsync(phis + (size_t)t * phiB, c.phit, phiB, cudaMemcpyDeviceToDevice, c.s);
+  }
+  cudaEventRecord(ev[1], c.s);
+  cudaMemcpyAsync(keep_rho, c.rho, e * 2 * N, cudaMemcpyDeviceToDevice, c.s);
+  cudaMemcpyAsync(keep_eps, c.eps, e * N, cudaMemcpyDeviceToDevice, c.s);
+  cudaMemcpyAsync(keep_q, c.q, e * N, cudaMemcpyDeviceToDevice, c.s);
+  cudaMemcpyAsync(keep_u, c.u, e * 3 * N, cudaMemcpyDeviceToDevice, c.s);
+
+  // objective and its adjoint seed at the final state
+  double v[kObsLen];
+  if (obs_sums(h, v) != LBEH_OK) return finish(cuda_fail(h, "adjoint objective"));
+  double mom[4] = {0, 0, 0, 0}, D = 0.0;
+  if (v[8] > 0) {
+    const double W = v[8], X = v[9] / W, Z = v[11] / W;
+    const double mxx = v[12] - W * X * X, mzz = v[13] - W * Z * Z;
+    const double ax = std::sqrt(mxx > 0 ? mxx : 0), bz = std::sqrt(mzz > 0 ? mzz : 0);
+    D = (ax + bz) > 0 ? (bz - ax) / (bz + ax) : 0.0;
+    mom[0] = X;
+    mom[1] = Z;
+    mom[2] = ax;
+    mom[3] = bz;
+  }
+  std::vector<void *> tmp;
+  cudaMemsetAsync(fb[0], 0, popB, c.s);
+  if (ionB) cudaMemsetAsync(nbf[0], 0, ionB, c.s);
+  if (seed->f_bar) {
+    const double *s = stage_in(h, seed->f_bar, LBEH_F64, seed->on_device, 38 * N, tmp);
+    if (!s) return finish(LBEH_ERR_OOM);
+    to_compute(h, s, fb[0], 38 * N);
+  }
+  if (seed->n_bar && ionB) {
+    const double *s = stage_in(h, seed->n_bar, LBEH_F64, seed->on_device, 2 * N, tmp);
+    if (!s) return finish(LBEH_ERR_OOM);
+    to_compute(h, s, nbf[0], 2 * N);
+  }
+  if (seed->d_deformation != 0.0 && v[8] > 0) A.seed(c, c.f[c.cur], fb[0], mom, seed->d_deformation);
+  cudaMemsetAsync(acc, 0, 8 * 16, c.s);
+
+  // reverse sweep, segment by segment from the last
+  int cur = 0;
+  long long cycles = 0;
+  auto step_ctx = [&](int t, int j) {
+    Ctx cc = c;
+    cc.f[0] = seg + (size_t)j * stB;
+    cc.f[1] = seg + (size_t)(j + 1) * stB;
+    cc.cur = 0;
+    if (ionB) {
+      cc.n[0] = seg + (size_t)j * stB + popB;
+      cc.n[1] = seg + (size_t)(j + 1) * stB + popB;
+    }
+    cc.ncur = 0;
+    cc.phit = phis + (size_t)t * phiB;
+    if (c.prec == LBEH_FP64) cc.phi = (double *)cc.phit;
+    return cc;
+  };
+  for (int sg = nseg - 1; sg >= 0; --sg) {
+    const int ts = sg * K, L = std::min(nsteps, ts + K) - ts;
+    cudaMemcpyAsync(seg, ck + (size_t)sg * stB, stB, cudaMemcpyDeviceToDevice, c.s);
+    for (int j = 0; j + 1 < L; ++j) {
+      Ctx cc = step_ctx(ts + j, j);
+      h->ops.macro(cc);
+      h->ops.collide(cc);
+      if (ionB) h->ops.np(cc);
+    }
+    for (int j = L - 1; j >= 0; --j) {
+      Ctx cc = step_ctx(ts + j, j);
+      h->ops.macro(cc);
+      h->ops.collide(cc);  // fields of the step: rho, J, psi, eps, q, u, face fluxes
+      a.f = cc.f[0];
+      a.n = ionB ? cc.n[0] : nullptr;
+      a.rho = c.rho;
+      a.J = c.J;
+      a.psi = c.psi;
+      a.eps = c.eps;
+      a.phi = cc.phit;
+      a.u = c.u;
+      a.flux = c.flux;
+      a.fbo = fb[cur];
+      a.fbn = fb[cur ^ 1];
+      a.nbo = nbf[cur];
+      a.nbn = nbf[cur ^ 1];
+      a.rb = rb;
+      a.Jb = Jb;
+      a.Felb = Felb;
+      a.KC = KC;
+      a.Sb = Sb;
+      a.psib = psib;
+      a.epsb = epsb;
+      a.Fb = Fb;
+      a.Efb = Efb;
+      a.Eb = Eb;
+      a.qadj = qadj;
+      a.lam = lam;
+      cudaMemsetAsync(part, 0, 8 * (size_t)kAdjBlocks * kAdjPar, c.s);
+      A.before_solve(cc, a, part);
+      if (c.has_field) {
+        double rr = 0.0;
+        const int it = poisson_solve(h->adj_pois, ca, &rr);
+        if (it == -1) return finish(cuda_fail(h, "adjoint Poisson solve"));
+        if (it < -1) {
+          worst = LBEH_ERR_POISSON_NOT_CONVERGED;
+          cycles += -it - 2;
+        } else {
+          cycles += it;
+        }
+      }
+      A.after_solve(cc, a, part);
+      reduce_partials_final(part, kAdjBlocks, kAdjPar, acc + 8, c.s);
+      count_launch(), k_add<<<1, 32, 0, c.s>>>(acc, acc + 8, kAdjPar);
+      cur ^= 1;
+    }
+  }
+  cudaEventRecord(ev[2], c.s);
+  cudaMemcpyAsync(c.rho, keep_rho, e * 2 * N, cudaMemcpyDeviceToDevice, c.s);
+  cudaMemcpyAsync(c.eps, keep_eps, e * N, cudaMemcpyDeviceToDevice, c.s);
+  cudaMemcpyAsync(c.q, keep_q, e * N, cudaMemcpyDeviceToDevice, c.s);
+  cudaMemcpyAsync(c.u, keep_u, e * 3 * N, cudaMemcpyDeviceToDevice, c.s);
+
+  // results
+  double hacc[kAdjPar];
+  cudaMemcpyAsync(hacc, acc, sizeof(hacc), cudaMemcpyDeviceToHost, c.s);
+  if (cudaStreamSynchronize(c.s) != cudaSuccess) return finish(cuda_fail(h, "adjoint sweep"));
+  out->deformation = D;
+  for (int k = 0; k < 3; ++k) out->dE_ext[k] = hacc[k];
+  out->dG = hacc[3];
+  out->dQ = 0.0;
+  const double *n0 = nullptr;
+  if (ionB) {
+    n0 = as_f64(h, nbf[cur], 2 * N, tmp);
+    if (!n0) return finish(LBEH_ERR_OOM);
+  }
+  if (dn_user && n0) {
+    const double *dn = stage_in(h, dn_user, LBEH_F64, out_dev, 2 * N, tmp);
+    if (!dn) return finish(LBEH_ERR_OOM);
+    out->dQ = dot_f64(n0, dn, 2 * N, c.red, c.s);
+  }
+  if (n0_user) {
+    if (n0) {
+      if (!stage_out(h, n0, n0_user, LBEH_F64, out_dev, 2 * N, tmp)) return finish(LBEH_ERR_CUDA);
+    } else if (out_dev) {
+      cudaMemsetAsync(n0_user, 0, 8 * 2 * N, c.s);
+    } else {
+      std::memset(n0_user, 0, 8 * 2 * N);
+    }
+  }
+  if (f0_user) {
+    const double *f0 = as_f64(h, fb[cur], 38 * N, tmp);
+    if (!f0 || !stage_out(h, f0, f0_user, LBEH_F64, out_dev, 38 * N, tmp)) return finish(LBEH_ERR_CUDA);
+  }
+  free_tmp(h, tmp);
+  float ms1 = 0.f, ms2 = 0.f;
+  cudaEventElapsedTime(&ms1, ev[0], ev[1]);
+  cudaEventElapsedTime(&ms2, ev[1], ev[2]);
+  out->forward_ms = ms1;
+  out->adjoint_ms = ms2;
+  out->adjoint_poisson_cycles = cycles;
+  if (cudaPeekAtLastError() != cudaSuccess) return finish(cuda_fail(h, "adjoint"));
+  return finish(worst);
 }
 
 int lbeh_get_fields(lbeh_handle *h, lbeh_fields *out) {

@@ -77,6 +77,17 @@ class lbeh_obs(C.Structure):
     ]
 
 
+class lbeh_obs_seed(C.Structure):
+    _fields_ = [("d_deformation", C.c_double), ("f_bar", C.c_void_p), ("n_bar", C.c_void_p),
+                ("on_device", C.c_int)]
+
+
+class lbeh_grads(C.Structure):
+    _fields_ = [("deformation", C.c_double), ("dE_ext", C.c_double * 3), ("dG", C.c_double), ("dQ", C.c_double),
+                ("dn0_dQ", C.c_void_p), ("f0_bar", C.c_void_p), ("n0_bar", C.c_void_p), ("on_device", C.c_int),
+                ("forward_ms", C.c_double), ("adjoint_ms", C.c_double), ("adjoint_poisson_cycles", C.c_longlong)]
+
+
 class lbeh_profile(C.Structure):
     _fields_ = [("ms", C.c_double * LBEH_NSTAGES), ("calls", C.c_longlong * LBEH_NSTAGES),
                 ("launches", C.c_longlong), ("poisson_cycles", C.c_longlong)]
@@ -103,6 +114,7 @@ def _load():
     lib.lbeh_batch_tune.argtypes = [H, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     lib.lbeh_batch_set_shape.argtypes = [H, C.c_int]
     lib.lbeh_batch_shape.argtypes = [H]
+    lib.lbeh_step_adjoint.argtypes = [H, C.c_int, C.c_int, C.POINTER(lbeh_obs_seed), C.POINTER(lbeh_grads)]
     lib.lbeh_destroy.argtypes = [H]
     lib.lbeh_destroy.restype = None
     lib.lbeh_last_error.argtypes = [H]
@@ -112,7 +124,7 @@ def _load():
     for name in ("lbeh_create", "lbeh_set_fields", "lbeh_get_fields", "lbeh_step", "lbeh_observables",
                  "lbeh_get_aux", "lbeh_profile_enable", "lbeh_profile_read", "lbeh_observables_noalloc",
                  "lbeh_create_batch", "lbeh_batch_box", "lbeh_batch_step_sequential", "lbeh_batch_tune",
-                 "lbeh_batch_set_shape", "lbeh_batch_shape"):
+                 "lbeh_batch_set_shape", "lbeh_batch_shape", "lbeh_step_adjoint"):
         getattr(lib, name).restype = C.c_int
     return lib
 
@@ -195,6 +207,13 @@ def lbeh_observables_noalloc(nx, ny, nz, ncomp, nions, dtype, f_ptr, n_ptr=None,
                                          n_ptr, solid_ptr, qc_ptr, C.byref(o), int(stream) or None),
            "lbeh_observables_noalloc")
     return o
+
+
+def lbeh_step_adjoint(h, nsteps: int, ckpt_every: int, seed: lbeh_obs_seed, grads: lbeh_grads) -> int:
+    rc = _lib.lbeh_step_adjoint(h, int(nsteps), int(ckpt_every), C.byref(seed), C.byref(grads))
+    if rc not in (LBEH_OK, LBEH_ERR_POISSON_NOT_CONVERGED):
+        raise LbehError(rc, "lbeh_step_adjoint [%s]" % lbeh_last_error(h))
+    return rc
 
 
 def lbeh_create_batch(params_list) -> C.c_void_p:
@@ -360,6 +379,38 @@ class System:
 
     def observables(self) -> lbeh_obs:
         return lbeh_observables(self.h)
+
+    def step_adjoint(self, nsteps: int, ckpt_every: int, d_deformation: float = 1.0, f_bar=None, n_bar=None,
+                     dn0_dQ=None, want_state: bool = False) -> dict:
+        """Advance nsteps and return the gradients of the objective (host FP64
+        arrays in, host FP64 arrays out)."""
+        keep = []
+
+        def host(a):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            keep.append(a)
+            return a.ctypes.data
+
+        seed = lbeh_obs_seed()
+        seed.d_deformation = float(d_deformation)
+        seed.f_bar = host(f_bar)
+        seed.n_bar = host(n_bar)
+        seed.on_device = 0
+        g = lbeh_grads()
+        g.dn0_dQ = host(dn0_dQ)
+        g.on_device = 0
+        out = {}
+        if want_state:
+            out["f0_bar"] = np.zeros((self.ncomp, 19) + self.shape)
+            g.f0_bar = out["f0_bar"].ctypes.data
+            out["n0_bar"] = np.zeros((2,) + self.shape)
+            g.n0_bar = out["n0_bar"].ctypes.data
+        out["status"] = lbeh_step_adjoint(self.h, nsteps, ckpt_every, seed, g)
+        out.update(deformation=g.deformation, dE_ext=np.array(g.dE_ext[:]), dG=g.dG, dQ=g.dQ,
+                   forward_ms=g.forward_ms, adjoint_ms=g.adjoint_ms, adjoint_poisson_cycles=g.adjoint_poisson_cycles)
+        return out
 
     def profile_enable(self, on: bool = True):
         lbeh_profile_enable(self.h, on)
