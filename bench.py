@@ -41,6 +41,15 @@ _FIELDS = (2 + 3 + 2 + 1 + 1 + 2) * 4 + (3 + 6) * 4
 COLLIDE_BYTES = {"fp32": 2 * 19 * 4 * 2 + _FIELDS, "bf16": 2 * 19 * 2 * 2 + _FIELDS}
 
 
+def collide_bytes(ncomp, pop_bytes, solids):
+    """Algorithmic bytes per site of k_collide with ions and a field: populations
+    read + written, rho (ncomp), J (3), psi (two components only), eps, phi,
+    n+ n- read once, psi_f and the solid mask with colloids; u (3) and the three
+    owned face fluxes per species written."""
+    reads = ncomp + 3 + (2 if ncomp == 2 else 0) + 1 + 1 + 2 + (1 if solids else 0)
+    return ncomp * 19 * pop_bytes * 2 + reads * 4 + (1 if solids else 0) + (3 + 6) * 4
+
+
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -296,6 +305,11 @@ def run_ours(args):
 
     if rank != 0:
         return
+    extra = {}
+    if not args.no_extra:
+        extra["suspension"] = suspension_run(lbeh, stream, peak, peak_kind, args)
+        extra["batch"] = batch_run(lbeh, stream, args)
+        extra["adjoint"] = adjoint_run(lbeh, stream, args)
     cpu = None if args.no_cpu_baseline else cpu_baseline(n)
     clocks = sampler.summary() if sampler else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
     total_ms = sum(prof["ms"].values())
@@ -318,7 +332,99 @@ def run_ours(args):
         "poisson_cycles_per_step": results["fp32"]["cycles"] / args.steps,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": prof["launches"],
     }
+    line.update(extra)
     print(json.dumps(line), flush=True)
+
+
+def _timed(step, stream, steps):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    rc = step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), rc
+
+
+def suspension_run(lbeh, stream, peak, peak_kind, args, n=256, steps=100):
+    """256^3 electrophoresis suspension: one fluid, 1e-3 salt, 200 moving
+    charged spheres of radius 6, E_x = 1e-3; FP32 and BF16 storage."""
+    import numpy as np
+    import synth
+    out = {"workload": "suspension %d^3, 200 moving colloids r=6, salt 1e-3, E_x=1e-3" % n, "steps": steps}
+    vx = {}
+    for prec in ("fp32", "bf16"):
+        w = synth.suspension(n=n, ncoll=200, r=6.0, prec=prec)
+        s = lbeh.System(w.params, stream.cuda_stream)
+        s.set_fields(rho=list(w.rho), n=list(w.n), colloid_x=w.colloid_x, colloid_v=w.colloid_v,
+                     colloid_q=w.colloid_q, colloid_r=w.colloid_r)
+        s.step(5)
+        ms, rc = _timed(s.step, stream, steps)
+        s.profile_enable(True)
+        s.step(min(steps, 50))
+        prof = s.profile_read()
+        s.profile_enable(False)
+        vx[prec] = np.array(s.get(("rho",))["cv"])[:, 0]
+        s.close()
+        t_coll = prof["ms"]["collide"] / max(1, prof["calls"]["collide"]) * 1e-3
+        gbs = collide_bytes(1, 4 if prec == "fp32" else 2, True) * n ** 3 / t_coll / 1e9
+        total = sum(prof["ms"].values())
+        out[prec] = {"mlups": n ** 3 * steps / (ms * 1e3), "ms_per_step": ms / steps, "status": rc,
+                     "collide_gbs": gbs, "collide_frac": gbs / peak, "peak_kind": peak_kind,
+                     "stage_share": {k: (v / total if total else None) for k, v in prof["ms"].items()}}
+    out["bf16_speedup"] = out["bf16"]["mlups"] / out["fp32"]["mlups"]
+    out["bf16_colloid_vx_rel_dev"] = float(np.abs(vx["bf16"] - vx["fp32"]).max() / max(np.abs(vx["fp32"]).max(), 1e-30))
+    return out
+
+
+def batch_run(lbeh, stream, args, steps=50):
+    """96 independent charged droplets (edges 32..64) in one cluster launch per
+    step call, against the single-system kernels stepping the boxes in turn."""
+    import synth
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    ws = synth.batch_boxes(nbox=96, steps=steps)
+    sites = sum(w.params.nx * w.params.ny * w.params.nz for w in ws)
+    bt = lbeh.Batch([w.params for w in ws], stream.cuda_stream)
+    for box, w in zip(bt.boxes, ws):
+        box.set_fields(rho=list(w.rho), n=list(w.n))
+    shape, _ = bt.tune(4)
+    bt.step(3)
+    ms, rc = _timed(bt.step, stream, steps)
+    bt.close()
+    singles = []
+    for w in ws:
+        s = lbeh.System(w.params, stream.cuda_stream)
+        s.set_fields(rho=list(w.rho), n=list(w.n))
+        s.step(2)
+        singles.append(s)
+    k = 5
+    ms_seq, _ = _timed(lambda m: [s.step(m) for s in singles], stream, k)
+    for s in singles:
+        s.close()
+    return {"workload": "96 charged droplets, edges {32..64}, FP32", "sites": sites, "steps": steps,
+            "cluster_blocks": shape, "mlups": sites * steps / (ms * 1e3), "ms_per_step": ms / steps,
+            "status": rc, "single_system_in_turn_mlups": sites * k / (ms_seq * 1e3),
+            "speedup_vs_single_system_in_turn": (sites * steps / ms) / (sites * k / ms_seq)}
+
+
+def adjoint_run(lbeh, stream, args, n=96, steps=800, ckpt=50):
+    """Gradient of the drop deformation after 800 steps (96^3, r=18, Q=50,
+    E_z=1.5e-3, FP32, checkpoints every 50) by the discrete adjoint."""
+    import synth
+    w = synth.droplet(n=n, r=18.0, seed=4, prec="fp32", salt=1e-3, Ez=1.5e-3, charge=50.0, steps=steps)
+    one = synth.droplet(n=n, r=18.0, seed=4, prec="fp32", salt=1e-3, Ez=1.5e-3, charge=1.0)
+    zero = synth.droplet(n=n, r=18.0, seed=4, prec="fp32", salt=1e-3, Ez=1.5e-3, charge=0.0)
+    s = lbeh.System(w.params, stream.cuda_stream)
+    s.set_fields(rho=list(w.rho), n=list(w.n))
+    g = s.step_adjoint(steps, ckpt, d_deformation=1.0, dn0_dQ=one.n - zero.n)
+    s.close()
+    return {"workload": "adjoint drop %d^3 r=18 Q=50 E_z=1.5e-3, %d steps, checkpoints every %d, FP32" % (n, steps, ckpt),
+            "forward_ms": g["forward_ms"], "reverse_ms": g["adjoint_ms"],
+            "reverse_over_forward": g["adjoint_ms"] / g["forward_ms"], "deformation": g["deformation"],
+            "dD_dEz": float(g["dE_ext"][2]), "dD_dG": g["dG"], "dD_dQ": g["dQ"], "status": g["status"],
+            "adjoint_poisson_cycles": g["adjoint_poisson_cycles"]}
 
 
 def main():
@@ -329,6 +435,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the suspension, batch and adjoint measurements")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -144,3 +144,26 @@ def test_fp32_adjoint_close_to_fp64(lbeh):
         s.close()
     assert abs(g["fp32"]["dE_ext"][2] - g["fp64"]["dE_ext"][2]) <= 1e-3 * abs(g["fp64"]["dE_ext"][2])
     assert abs(g["fp32"]["dG"] - g["fp64"]["dG"]) <= 1e-2 * abs(g["fp64"]["dG"])
+
+
+def test_autograd_function_returns_the_adjoint_gradients(lbeh):
+    torch = pytest.importorskip("torch")
+    from paper_1712_08494_gb300.autograd import deformation
+    nsteps = 5
+    dn = _drop(Q=1.0).n - _drop(Q=0.0).n
+
+    def factory(E, G, Q):
+        w = _drop(Ez=E[2], G=G, Q=Q)
+        return _sys(lbeh, w)
+
+    E = torch.tensor([0.0, 0.0, 2e-2], dtype=torch.float64, requires_grad=True)
+    G = torch.tensor(4.0, dtype=torch.float64, requires_grad=True)
+    Q = torch.tensor(5.0, dtype=torch.float64, requires_grad=True)
+    D = deformation(factory, E, G, Q, nsteps, 2, dn)
+    (3.0 * D).backward()
+    s = factory([0.0, 0.0, 2e-2], 4.0, 5.0)
+    g = s.step_adjoint(nsteps, 2, d_deformation=1.0, dn0_dQ=dn)
+    s.close()
+    assert float(D) == g["deformation"]
+    assert np.allclose(E.grad.numpy(), 3.0 * g["dE_ext"], rtol=0, atol=0)
+    assert float(G.grad) == 3.0 * g["dG"] and float(Q.grad) == 3.0 * g["dQ"]
