@@ -20,38 +20,50 @@ __device__ __forceinline__ double min_image_d(double d, int n) {
   return d;
 }
 
-__global__ void k_colloid_forces_move(Dims dm, int nc, double *__restrict__ cx, double *__restrict__ cv,
-                                      const double *__restrict__ cr, double *__restrict__ cforce, double rho_p,
-                                      double k_hertz, double eta, int moving) {
+// Pair forces on colloid i (block i, partners strided over the threads,
+// fixed-order block sum), added to the force of the step.
+__global__ void __launch_bounds__(128) k_colloid_pairs(Dims dm, int nc, const double *__restrict__ cx,
+                                                       const double *__restrict__ cv, const double *__restrict__ cr,
+                                                       double *__restrict__ cforce, double k_hertz, double eta) {
+  const int i = blockIdx.x;
   const int dims[3] = {dm.nx, dm.ny, dm.nz};
-  // forces first (all colloids read the old positions and velocities)
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
-    double F[3] = {cforce[3 * i], cforce[3 * i + 1], cforce[3 * i + 2]};
-    for (int j = 0; j < nc; ++j) {
-      if (j == i) continue;
-      double dd[3];
-      for (int a = 0; a < 3; ++a) dd[a] = min_image_d(cx[3 * i + a] - cx[3 * j + a], dims[a]);
-      const double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
-      if (dist == 0.0) continue;
-      const double nh[3] = {dd[0] / dist, dd[1] / dist, dd[2] / dist};
-      const double overlap = cr[i] + cr[j] - dist;
-      if (overlap > 0.0) {
-        const double fh = k_hertz * pow(overlap, 1.5);
-        for (int a = 0; a < 3; ++a) F[a] += fh * nh[a];
-      }
-      const double gap = dist - (cr[i] + cr[j]);
-      if (gap > 0.0 && gap < 2.0 / 3.0) {
-        double vrel = 0.0;
-        for (int a = 0; a < 3; ++a) vrel += nh[a] * (cv[3 * i + a] - cv[3 * j + a]);
-        const double fl = -1.5 * M_PI * eta * cr[i] * cr[j] * vrel * (1.0 / gap - 1.0);
-        for (int a = 0; a < 3; ++a) F[a] += fl * nh[a];
-      }
+  double F[3] = {0.0, 0.0, 0.0};
+  for (int j = threadIdx.x; j < nc; j += blockDim.x) {
+    if (j == i) continue;
+    double dd[3];
+    for (int a = 0; a < 3; ++a) dd[a] = min_image_d(cx[3 * i + a] - cx[3 * j + a], dims[a]);
+    const double dist = sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+    if (dist == 0.0) continue;
+    const double nh[3] = {dd[0] / dist, dd[1] / dist, dd[2] / dist};
+    const double overlap = cr[i] + cr[j] - dist;
+    if (overlap > 0.0) {
+      const double fh = k_hertz * overlap * sqrt(overlap);
+      for (int a = 0; a < 3; ++a) F[a] += fh * nh[a];
     }
-    for (int a = 0; a < 3; ++a) cforce[3 * i + a] = F[a];
+    const double gap = dist - (cr[i] + cr[j]);
+    if (gap > 0.0 && gap < 2.0 / 3.0) {
+      double vrel = 0.0;
+      for (int a = 0; a < 3; ++a) vrel += nh[a] * (cv[3 * i + a] - cv[3 * j + a]);
+      const double fl = -1.5 * M_PI * eta * cr[i] * cr[j] * vrel * (1.0 / gap - 1.0);
+      for (int a = 0; a < 3; ++a) F[a] += fl * nh[a];
+    }
   }
+  __shared__ double sh[3][128];
+  for (int a = 0; a < 3; ++a) sh[a][threadIdx.x] = F[a];
   __syncthreads();
-  if (!moving) return;
-  for (int i = threadIdx.x; i < nc; i += blockDim.x) {
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+      for (int a = 0; a < 3; ++a) sh[a][threadIdx.x] += sh[a][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) cforce[3 * i + threadIdx.x] += sh[threadIdx.x][0];
+}
+
+// velocity-Verlet with the step's force held over the step
+__global__ void k_colloid_move(Dims dm, int nc, double *__restrict__ cx, double *__restrict__ cv,
+                               const double *__restrict__ cr, const double *__restrict__ cforce, double rho_p) {
+  const int dims[3] = {dm.nx, dm.ny, dm.nz};
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x) {
     const double m = rho_p * (4.0 / 3.0) * M_PI * cr[i] * cr[i] * cr[i];
     for (int a = 0; a < 3; ++a) {
       const double acc = cforce[3 * i + a] / m;
@@ -75,8 +87,10 @@ __global__ void k_colloid_apply_dp(int nc, double *__restrict__ cv, const double
 void colloid_forces_move(Ctx &c) {
   if (c.ncoll == 0) return;
   const double eta = (c.tau - 0.5) / 3.0;
-  count_launch(), k_colloid_forces_move<<<1, 256, 0, c.s>>>(c.d, c.ncoll, c.cx, c.cv, c.cr, c.cforce, c.rho_p,
-                                                            c.k_hertz, eta, c.moving ? 1 : 0);
+  count_launch(), k_colloid_pairs<<<c.ncoll, 128, 0, c.s>>>(c.d, c.ncoll, c.cx, c.cv, c.cr, c.cforce, c.k_hertz, eta);
+  if (c.moving)
+    count_launch(), k_colloid_move<<<grid_for(c.ncoll, 128), 128, 0, c.s>>>(c.d, c.ncoll, c.cx, c.cv, c.cr, c.cforce,
+                                                                          c.rho_p);
 }
 
 void colloid_apply_dp(Ctx &c) {

@@ -57,22 +57,39 @@ __global__ void k_project(Dims d, int h, const double *__restrict__ cx, const do
   const long long tot = (long long)b.cnt[0] * b.cnt[1] * b.cnt[2];
   const int hp = h + 1;
   const double inv = double(hp) * hp * hp;
+  // sub-cube centre offsets (k + 1/2)/(h+1) - 1/2, once per block
+  __shared__ double off[16];
+  if (threadIdx.x < hp) off[threadIdx.x] = __dsub_rn(__ddiv_rn(threadIdx.x + 0.5, double(hp)), 0.5);
+  __syncthreads();
+  // Every sub-cube centre lies within sqrt(3)/2 < 0.87 of the node.  A node
+  // farther than that margin (plus a relative 1e-9, far above the rounding
+  // of the squared distances) from the sphere surface has all its samples on
+  // one side, so the count is (h+1)^3 or 0 without sampling: the same count
+  // the rounded per-sample test gives.
+  // (used only where every sample and the node share one periodic image)
+  const double r_in = r - 0.87 - 1e-9 * r, r_out = r + 0.87 + 1e-9 * r;
+  const bool shortcut = 2.0 * (r_out + 1.0) < double(min(d.nx, min(d.ny, d.nz)));
   for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
     int x, y, z;
     box_site(d, b, t, x, y, z);
     const long long i = site(d, x, y, z);
-    if (dist2(double(x), double(y), double(z), X, d) < r2) {
+    const double d2 = dist2(double(x), double(y), double(z), X, d);
+    if (d2 < r2) {
       solid[i] = 1;
       atomicMax(owner + i, j);
     }
     int nu = 0;
-    for (int kz = 0; kz < hp; ++kz) {
-      const double oz = __dsub_rn(__ddiv_rn(kz + 0.5, double(hp)), 0.5);
-      for (int ky = 0; ky < hp; ++ky) {
-        const double oy = __dsub_rn(__ddiv_rn(ky + 0.5, double(hp)), 0.5);
-        for (int kx = 0; kx < hp; ++kx) {
-          const double ox = __dsub_rn(__ddiv_rn(kx + 0.5, double(hp)), 0.5);
-          if (dist2(__dadd_rn(double(x), ox), __dadd_rn(double(y), oy), __dadd_rn(double(z), oz), X, d) < r2) ++nu;
+    if (shortcut && r_in > 0.0 && d2 < r_in * r_in) {
+      nu = hp * hp * hp;
+    } else if (shortcut && d2 > r_out * r_out) {
+      nu = 0;
+    } else {
+      for (int kz = 0; kz < hp; ++kz) {
+        const double pz = __dadd_rn(double(z), off[kz]);
+        for (int ky = 0; ky < hp; ++ky) {
+          const double py = __dadd_rn(double(y), off[ky]);
+          for (int kx = 0; kx < hp; ++kx)
+            if (dist2(__dadd_rn(double(x), off[kx]), py, pz, X, d) < r2) ++nu;
         }
       }
     }

@@ -60,6 +60,8 @@ struct Ctx {
   double *cx = nullptr, *cv = nullptr, *cq = nullptr, *cr = nullptr;  // device colloid table
   double *cforce = nullptr;  // [ncoll][3] total force of the step
   double *cdp = nullptr;     // [ncoll][3] momentum change of the remap
+  void *remap_share = nullptr;    // [2][N] ion share of each covered node (moving colloids with ions)
+  uint8_t *remap_flag = nullptr;  // [N] receives a share this remap (kept zero between remaps)
   bool moving = false;
   double rho_p = 5.0, k_hertz = 1.0;
   int *ccount = nullptr;     // [ncoll] surface node counts

@@ -426,6 +426,10 @@ int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
   if (c.moving) {
     ok &= (c.solid_old = (uint8_t *)dalloc(h, N)) != nullptr;
     ok &= (c.owner_old = (int *)dalloc(h, 4 * N)) != nullptr;
+    if (p->nions) {
+      ok &= (c.remap_share = dalloc(h, T * 2 * N)) != nullptr;
+      ok &= (c.remap_flag = (uint8_t *)dalloc(h, N)) != nullptr;
+    }
   }
   ok &= (c.ccount = (int *)dalloc(h, 4 * nc)) != nullptr;
   ok &= (c.status = (int *)dalloc(h, sizeof(int))) != nullptr;
@@ -454,6 +458,7 @@ int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
     cudaMemsetAsync(c.phi_lo, 0, 4 * N, c.s);
   }
   cudaMemsetAsync(c.status, 0, sizeof(int), c.s);
+  if (c.remap_flag) cudaMemsetAsync(c.remap_flag, 0, N, c.s);
   cudaMemsetAsync(c.cv, 0, 8 * 3 * nc, c.s);
   cudaMemsetAsync(c.cforce, 0, 8 * 3 * nc, c.s);
   if (p->nions) {

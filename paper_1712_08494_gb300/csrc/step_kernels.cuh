@@ -805,15 +805,56 @@ __global__ void k_remap(StepK<T> k, S *__restrict__ f, const uint8_t *__restrict
 }
 
 // Ions of covered nodes go in equal shares to their D3Q19 neighbours that are
-// fluid before and after the move (gathered by the receivers, fixed order).
+// fluid before and after the move.  Pass 1 (one block per colloid, its new
+// bounding box): each covered node stores its share n/m (m kept neighbours),
+// clears its own ions and flags its kept neighbours.  Pass 2 (whole lattice,
+// a flag byte per site): flagged nodes gather the shares of their covered
+// neighbours in a fixed order and clear the flag.
+template <typename T>
+__global__ void k_remap_mark(StepK<T> k, T *__restrict__ n, const uint8_t *__restrict__ solid,
+                             const uint8_t *__restrict__ solid_old, const int *__restrict__ owner,
+                             const double *__restrict__ ccx, const double *__restrict__ ccr, T *__restrict__ share,
+                             uint8_t *__restrict__ flag) {
+  const int j = blockIdx.x;
+  const Dims d = k.d;
+  const long long N = d.N;
+  int lo[3], cnt[3];
+  const int dims[3] = {d.nx, d.ny, d.nz};
+  for (int a = 0; a < 3; ++a) {
+    const double X = ccx[3 * j + a], r = ccr[j];
+    lo[a] = int(ceil(X - r - 2.0));
+    const int hi = int(floor(X + r + 2.0));
+    cnt[a] = min(dims[a], hi - lo[a] + 1);
+  }
+  const long long tot = (long long)cnt[0] * cnt[1] * cnt[2];
+  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+    const int x = ((lo[0] + int(t % cnt[0])) % d.nx + d.nx) % d.nx;
+    const int y = ((lo[1] + int((t / cnt[0]) % cnt[1])) % d.ny + d.ny) % d.ny;
+    const int z = ((lo[2] + int(t / ((long long)cnt[0] * cnt[1]))) % d.nz + d.nz) % d.nz;
+    const long long src = site(d, x, y, z);
+    if (!(solid[src] && !solid_old[src] && owner[src] == j)) continue;
+    long long sn[19];
+    neighbours19(d, x, y, z, sn);
+    int m = 0;
+    for (int q2 = 1; q2 < 19; ++q2) m += (!solid[sn[q2]] && !solid_old[sn[q2]]) ? 1 : 0;
+    for (int s = 0; s < 2; ++s) {
+      share[s * N + src] = m > 0 ? n[s * N + src] / T(m) : T(0);
+      n[s * N + src] = T(0);
+    }
+    for (int q2 = 1; q2 < 19; ++q2)
+      if (!solid[sn[q2]] && !solid_old[sn[q2]]) flag[sn[q2]] = 1;
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_remap_ions(StepK<T> k, T *__restrict__ n, const uint8_t *__restrict__ solid,
-                                                    const uint8_t *__restrict__ solid_old) {
+                                                    const uint8_t *__restrict__ solid_old,
+                                                    const T *__restrict__ share, uint8_t *__restrict__ flag) {
   const Dims d = k.d;
   const long long N = d.N;
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= N) return;
-  if (solid[i] || solid_old[i]) return;
+  if (i >= N || !flag[i]) return;
+  flag[i] = 0;
   int x, y, z;
   coords(d, i, x, y, z);
   long long nb[19];
@@ -822,25 +863,10 @@ __global__ void __launch_bounds__(256) k_remap_ions(StepK<T> k, T *__restrict__ 
   for (int qd = 1; qd < 19; ++qd) {
     const long long src = nb[opp(qd)];  // node i - c_q sends along c_q to i
     if (!(solid[src] && !solid_old[src])) continue;
-    int sx, sy, sz;
-    coords(d, src, sx, sy, sz);
-    long long sn[19];
-    neighbours19(d, sx, sy, sz, sn);
-    int m = 0;
-    for (int q2 = 1; q2 < 19; ++q2) m += (!solid[sn[q2]] && !solid_old[sn[q2]]) ? 1 : 0;
-    if (m == 0) continue;
-    for (int s = 0; s < 2; ++s) add[s] += n[s * N + src] / T(m);
+    for (int s = 0; s < 2; ++s) add[s] += share[s * N + src];
   }
   n[i] += add[0];
   n[N + i] += add[1];
-}
-
-template <typename T>
-__global__ void k_zero_solid_ions(T *__restrict__ n, const uint8_t *__restrict__ solid, long long N) {
-  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= N || !solid[i]) return;
-  n[i] = T(0);
-  n[N + i] = T(0);
 }
 
 // ---------------------------------------------------------------- host launchers
@@ -961,8 +987,10 @@ template <typename S, typename T> struct Launch {
                                                                 c.cr, c.cv, c.cdp);
     if (c.nions) {
       T *n = (T *)c.n[c.ncur];
-      count_launch(), k_remap_ions<T><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, n, c.solid, c.solid_old);
-      count_launch(), k_zero_solid_ions<T><<<grid_for(c.d.N, B), B, 0, c.s>>>(n, c.solid, c.d.N);
+      count_launch(), k_remap_mark<T><<<c.ncoll, B, 0, c.s>>>(k, n, c.solid, c.solid_old, c.owner, c.cx, c.cr,
+                                                               (T *)c.remap_share, c.remap_flag);
+      count_launch(), k_remap_ions<T><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, n, c.solid, c.solid_old,
+                                                                          (const T *)c.remap_share, c.remap_flag);
     }
   }
   static PrecOps ops() {
