@@ -100,6 +100,27 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
   e = __fmaf_rn(a.lo, b.hi, e);
   return fast_two_sum(p, e);
 }
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+  DF s = two_sum(a.hi, b);
+  s.lo = __fadd_rn(s.lo, a.lo);
+  return fast_two_sum(s.hi, s.lo);
+}
+
+// Per-thread running sum: double-float words in the FP32 modes (site values
+// are FP32 and the FP64 pipe is slow), plain FP64 in the FP64 mode; the block
+// and grid reductions that follow run in FP64.
+template <bool DFM> struct SumAcc;
+template <> struct SumAcc<true> {
+  DF v{0.f, 0.f};
+  __device__ __forceinline__ void add(float x) { v = df_add_f(v, x); }
+  __device__ __forceinline__ double get() const { return double(v.hi) + double(v.lo); }
+};
+template <> struct SumAcc<false> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double get() const { return v; }
+};
+
 __host__ __device__ inline DF df_split(double v) {
   const float h = float(v);
   return DF{h, float(v - double(h))};
@@ -462,7 +483,7 @@ __device__ __forceinline__ double sum_partials(const double *part, int nb, doubl
 
 template <typename T, bool DFM>
 __device__ __forceinline__ void residual_site(const PArgs<T> &a, const Level<T> &L0, long long i, double qbar,
-                                              DF qbar_df, double &ar, double &ab, double &ap) {
+                                              DF qbar_df, SumAcc<DFM> &ar, SumAcc<DFM> &ab, SumAcc<DFM> &ap) {
   const Dims d = L0.dims();
   int x, y, z;
   coords(d, i, x, y, z);
@@ -487,9 +508,9 @@ __device__ __forceinline__ void residual_site(const PArgs<T> &a, const Level<T> 
     const DF r = df_sub(b, Ap);
     const float rf = __fadd_rn(r.hi, r.lo);
     L0.b[i] = T(rf);
-    ar += double(rf * rf);
-    ab += double(b.hi * b.hi);
-    ap += double(p.hi);
+    ar.add(rf * rf);
+    ab.add(b.hi * b.hi);
+    ap.add(p.hi);
   } else {
     const double *phi = a.phi;
     const double p = phi[i];
@@ -501,9 +522,9 @@ __device__ __forceinline__ void residual_site(const PArgs<T> &a, const Level<T> 
                       double(kym) * (p - phi[iym]) + double(kzp) * (phi[izp] - p) - double(kzm) * (p - phi[izm]);
     const double r = b - Ap;
     L0.b[i] = T(r);
-    ar += r * r;
-    ab += b * b;
-    ap += p;
+    ar.add(r * r);
+    ab.add(b * b);
+    ap.add(p);
   }
 }
 
@@ -512,11 +533,11 @@ template <typename T, bool DFM, class Team>
 __device__ bool residual_pass(const PArgs<T> &a, const Team &tm, const Level<T> &L0, double qbar, DF qbar_df,
                               double *sh, double &r2, double &b2, double &ps) {
   const long long G = tm.size();
-  double ar = 0.0, ab = 0.0, ap = 0.0;
-  for (long long i = tm.rank(); i < L0.N; i += G) residual_site<T, DFM>(a, L0, i, qbar, qbar_df, ar, ab, ap);
-  ar = block_sum_n(ar, sh);
-  ab = block_sum_n(ab, sh);
-  ap = block_sum_n(ap, sh);
+  SumAcc<DFM> sr, sb, sp;
+  for (long long i = tm.rank(); i < L0.N; i += G) residual_site<T, DFM>(a, L0, i, qbar, qbar_df, sr, sb, sp);
+  const double ar = block_sum_n(sr.get(), sh);
+  const double ab = block_sum_n(sb.get(), sh);
+  const double ap = block_sum_n(sp.get(), sh);
   const int nb = tm.nblocks();
   if (threadIdx.x == 0) {
     a.part[tm.block()] = ar;
@@ -546,7 +567,7 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
   const int have_prev = st->have_prev;
 
   // initial guess, level-0 face coefficients, sum of q
-  double accq = 0.0;
+  SumAcc<DFM> sq;
   for (long long i = gt; i < N; i += G) {
     if constexpr (DFM) {
       const DF p{a.phi_hi[i], a.phi_lo[i]};
@@ -570,9 +591,9 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
       L0.k[1][i] = T(0.5) * (e + a.eps[site(d, x, wrapp(y, d.ny), z)]);
       L0.k[2][i] = T(0.5) * (e + a.eps[site(d, x, y, wrapp(z, d.nz))]);
     }
-    accq += double(a.q[i]);
+    sq.add(a.q[i]);
   }
-  accq = block_sum_n(accq, sh);
+  const double accq = block_sum_n(sq.get(), sh);
   if (threadIdx.x == 0) a.part[tm.block()] = accq;
   if (!tm.sync()) return;
   const double qbar = sum_partials(a.part, tm.nblocks(), sh) / double(N);
@@ -680,7 +701,7 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
       // FP32 modes: r <- r - A e on the FP32 level-0 residual (its rounding error is
       // relative to |A e| ~ |r|), phi += e in double-float; the double-float residual
       // of the first pass fixes the starting point of each solve
-      double ar = 0.0, ap = 0.0;
+      SumAcc<DFM> sr, sp;
       for (long long i = gt; i < N; i += G) {
         int x, y, z;
         coords(d, i, x, y, z);
@@ -694,14 +715,14 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
                      fc.zp * (e[izp] - ei) + fc.zm * (e[izm] - ei);
         const T r = L0.b[i] - Ae;
         L0.b[i] = r;
-        ar += double(r * r);
+        sr.add(r * r);
         const DF s = df_add(DF{a.phi_hi[i], a.phi_lo[i]}, DF{float(ei), 0.f});
         a.phi_hi[i] = s.hi;
         a.phi_lo[i] = s.lo;
-        ap += double(s.hi);
+        sp.add(s.hi);
       }
-      ar = block_sum_n(ar, sh);
-      ap = block_sum_n(ap, sh);
+      const double ar = block_sum_n(sr.get(), sh);
+      const double ap = block_sum_n(sp.get(), sh);
       const int nb = tm.nblocks();
       if (threadIdx.x == 0) {
         a.part[tm.block()] = ar;
