@@ -55,6 +55,42 @@ def env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+class Ranks:
+    """Replica bookkeeping of a torchrun launch: one independent box per rank,
+    no collective on the data path; a barrier around the timed region and the
+    max of the per-rank times (nccl on GPUs, gloo on CPU)."""
+
+    def __init__(self, backend=None):
+        self.rank, self.world, self.local = env_rank()
+        self.dist = None
+        self.device = "cpu"
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            if backend is None:
+                backend = "nccl" if torch.cuda.is_available() else "gloo"
+            dist.init_process_group(backend)
+            self.dist = dist
+            self.device = "cuda" if backend == "nccl" else "cpu"
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, v):
+        if self.dist is None:
+            return v
+        import torch
+        t = torch.tensor([float(v)], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -203,23 +239,11 @@ def run_ours(args):
     pkg.build()
     lbeh = pkg.load()
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    ranks = Ranks()
     stream = torch.cuda.current_stream()
     n = args.size
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    barrier = ranks.barrier
+    max_over_ranks = ranks.max
 
     results = {}
     fields = {}
@@ -269,6 +293,8 @@ def run_ours(args):
     msbf = results["bf16"]["ms"]
     mlupsbf = world * N * args.steps / (msbf * 1e3)
     err_bf = max(float(np.abs(fields["bf16"][s] - fields["fp32"][s]).max() / np.abs(fields["fp32"][s]).max())
+                 for s in range(2))
+    rms_bf = max(float(np.sqrt(((fields["bf16"][s] - fields["fp32"][s]) ** 2).mean() / (fields["fp32"][s] ** 2).mean()))
                  for s in range(2))
 
     # end-to-end through the C-ABI with pinned host buffers: every step loads
@@ -322,7 +348,10 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (populations %.0f MB)" % (2 * 19 * 4 * N / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "bf16_storage": {"value": mlupsbf, "unit": "MLUPS", "speedup_vs_fp32": mlupsbf / mlups32,
-                         "max_rel_dev_rho_vs_fp32": err_bf, "ms_per_step": msbf / args.steps,
+                         "max_rel_dev_rho_vs_fp32": err_bf, "rms_rel_dev_rho_vs_fp32": rms_bf,
+                         "deformation_fp32": results["fp32"]["obs"].deformation,
+                         "deformation_bf16": results["bf16"]["obs"].deformation,
+                         "ms_per_step": msbf / args.steps,
                          "collide_gbs": achievedb},
         "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": tr,
