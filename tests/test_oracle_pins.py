@@ -384,6 +384,22 @@ def _brute_project(nx, ny, nz, X, R, h):
     return solid, np.minimum(psi, 1.0)
 
 
+def test_boxed_projection_equals_whole_lattice_projection():
+    """project_boxed (bounding boxes only) gives the same mask, owners and
+    solid fractions bit for bit, with spheres wrapping every face, touching
+    and overlapping spheres, and radii with sub-cube samples on the sphere."""
+    rng = np.random.default_rng(9)
+    nx, ny, nz = 18, 15, 21
+    X = np.array([[0.4, 14.7, 10.0], [17.2, 7.5, 0.3], [9.0, 7.5, 20.6], [9.0, 7.5, 12.0], [11.5, 8.0, 12.25]])
+    X = np.vstack([X, rng.uniform(0, 1, size=(4, 3)) * [nx, ny, nz]])
+    R = np.array([3.2, 2.7, 4.0, 2.5, 2.5, 1.9, 3.375, 2.0, 4.5])
+    for h in (1, 3):
+        a = geometry.project(nx, ny, nz, X, R, h)
+        b = geometry.project_boxed(nx, ny, nz, X, R, h)
+        for u, v in zip(a, b):
+            assert np.array_equal(u, v)
+
+
 def test_geometry_matches_brute_force_bit_exact():
     X = np.array([[1.3, 7.9, 4.25], [8.0, 3.0, 9.5]])   # first one wraps in x and y
     R = np.array([3.1, 2.5])
