@@ -181,7 +181,20 @@ __device__ __forceinline__ void jacobi_range(const Level<T> &L, T w, long long t
   }
 }
 
-// coarse b(I) = mean over children of the fine residual (b - A x)
+// diagonal of the level operator at cell I
+template <typename T> __device__ __forceinline__ T diag_at(const Level<T> &L, long long I, int X, int Y, int Z) {
+  const Dims c = L.dims();
+  const Faces<T> fc = faces(L, I, site(c, wrapp(X, c.nx), Y, Z), site(c, wrapm(X, c.nx), Y, Z),
+                            site(c, X, wrapp(Y, c.ny), Z), site(c, X, wrapm(Y, c.ny), Z), site(c, X, Y, wrapp(Z, c.nz)),
+                            site(c, X, Y, wrapm(Z, c.nz)));
+  return L.h[0] * (fc.xp + fc.xm) + L.h[1] * (fc.yp + fc.ym) + L.h[2] * (fc.zp + fc.zm);
+}
+
+// coarse b(I) = mean over children of the fine residual (b - A x).  After a
+// red-black sweep that ended with the black colour the residual vanishes on
+// black cells (each was just solved exactly for its equation), so only the
+// red children are evaluated.  The first half sweep on the coarse level
+// starts from x = 0, which sets its red cells to -b/diag: that is done here.
 template <typename T>
 __device__ __forceinline__ void restrict_range(const Level<T> &F, const Level<T> &C, long long t0, long long dt) {
   const Dims f = F.dims(), c = C.dims();
@@ -194,13 +207,16 @@ __device__ __forceinline__ void restrict_range(const Level<T> &F, const Level<T>
       for (int ty = 0; ty <= C.cf[1]; ++ty)
         for (int tx = 0; tx <= C.cf[0]; ++tx) {
           const int x = C.cf[0] ? 2 * X + tx : X, y = C.cf[1] ? 2 * Y + ty : Y, z = C.cf[2] ? 2 * Z + tz : Z;
+          ++cnt;
+          if (F.rb && ((x + y + z) & 1)) continue;
           const long long i = site(f, x, y, z);
           T off, diag;
           stencil(f, F, i, x, y, z, F.x, off, diag);
           acc += F.b[i] - (off - diag * F.x[i]);
-          ++cnt;
         }
-    C.b[I] = acc / T(cnt);
+    const T bI = acc / T(cnt);
+    C.b[I] = bI;
+    if (C.rb && !((X + Y + Z) & 1)) C.x[I] = -bI / diag_at(C, I, X, Y, Z);
   }
 }
 
@@ -209,6 +225,25 @@ template <typename T>
 __device__ __forceinline__ void prolong_range(const Level<T> &F, const Level<T> &C, long long t0, long long dt) {
   const Dims f = F.dims(), c = C.dims();
   const int cd[3] = {c.nx, c.ny, c.nz};
+  if (C.cf[0] && C.cf[1] && C.cf[2]) {
+    // coarsened along every axis: weights 27/64, 9/64, 3/64, 1/64
+    for (long long i = t0; i < f.N; i += dt) {
+      int x, y, z;
+      coords(f, i, x, y, z);
+      const int X0 = x >> 1, Y0 = y >> 1, Z0 = z >> 1;
+      const int X1 = (x & 1) ? (X0 + 1 == c.nx ? 0 : X0 + 1) : (X0 == 0 ? c.nx - 1 : X0 - 1);
+      const int Y1 = (y & 1) ? (Y0 + 1 == c.ny ? 0 : Y0 + 1) : (Y0 == 0 ? c.ny - 1 : Y0 - 1);
+      const int Z1 = (z & 1) ? (Z0 + 1 == c.nz ? 0 : Z0 + 1) : (Z0 == 0 ? c.nz - 1 : Z0 - 1);
+      const T *cx = C.x;
+      const T v000 = cx[site(c, X0, Y0, Z0)];
+      const T v100 = cx[site(c, X1, Y0, Z0)], v010 = cx[site(c, X0, Y1, Z0)], v001 = cx[site(c, X0, Y0, Z1)];
+      const T v110 = cx[site(c, X1, Y1, Z0)], v101 = cx[site(c, X1, Y0, Z1)], v011 = cx[site(c, X0, Y1, Z1)];
+      const T v111 = cx[site(c, X1, Y1, Z1)];
+      F.x[i] += T(0.421875) * v000 + T(0.140625) * ((v100 + v010) + v001) + T(0.046875) * ((v110 + v101) + v011) +
+                T(0.015625) * v111;
+    }
+    return;
+  }
   for (long long i = t0; i < f.N; i += dt) {
     int x, y, z;
     coords(f, i, x, y, z);
@@ -655,27 +690,25 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
       const Level<T> Ll = a.lv[l];
       const Level<T> Lc = a.lv[l + 1];
       for (int s = 0; s < kNu; ++s) {
-        if (s == 0) {
-          // first red half sweep from x = 0 (neighbours are black and still unset)
+        // first red half sweep from x = 0: x = -b/diag, done by the
+        // restriction that produced the right-hand side on coarse levels
+        if (s > 0) {
+          rb_range(Ll, 0, gt, G);
+          if (!tm.sync()) return;
+        } else if (l == 0) {
           const unsigned hx = unsigned(Ll.nx / 2);
+          const Dims dl = Ll.dims();
           for (long long t = gt; t < Ll.N / 2; t += G) {
             const unsigned r = unsigned(t) / hx;
             const int xh = int(unsigned(t) - r * hx);
             const int z = int(r / unsigned(Ll.ny));
             const int y = int(r - unsigned(z) * unsigned(Ll.ny));
             const int x = 2 * xh + ((y + z) & 1);
-            const Dims dl = Ll.dims();
             const long long i = site(dl, x, y, z);
-            const Faces<T> fc = faces(Ll, i, site(dl, wrapp(x, dl.nx), y, z), site(dl, wrapm(x, dl.nx), y, z),
-                                      site(dl, x, wrapp(y, dl.ny), z), site(dl, x, wrapm(y, dl.ny), z),
-                                      site(dl, x, y, wrapp(z, dl.nz)), site(dl, x, y, wrapm(z, dl.nz)));
-            const T diag = Ll.h[0] * (fc.xp + fc.xm) + Ll.h[1] * (fc.yp + fc.ym) + Ll.h[2] * (fc.zp + fc.zm);
-            Ll.x[i] = -Ll.b[i] / diag;
+            Ll.x[i] = -Ll.b[i] / diag_at(Ll, i, x, y, z);
           }
-        } else {
-          rb_range(Ll, 0, gt, G);
+          if (!tm.sync()) return;
         }
-        if (!tm.sync()) return;
         rb_range(Ll, 1, gt, G);
         if (!tm.sync()) return;
       }
@@ -701,19 +734,26 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
       // FP32 modes: r <- r - A e on the FP32 level-0 residual (its rounding error is
       // relative to |A e| ~ |r|), phi += e in double-float; the double-float residual
       // of the first pass fixes the starting point of each solve
+      // after the closing black half sweep the residual of the correction
+      // equation vanishes on black cells; only red cells form r - A e
+      const bool zero_black = L0.rb && a.tail > 0;
       SumAcc<DFM> sr, sp;
       for (long long i = gt; i < N; i += G) {
         int x, y, z;
         coords(d, i, x, y, z);
-        const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
-        const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
-        const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
+        const bool red = !((x + y + z) & 1);
         const T *e = L0.x;
         const T ei = e[i];
-        const Faces<T> fc = faces(L0, i, ixp, ixm, iyp, iym, izp, izm);
-        const T Ae = fc.xp * (e[ixp] - ei) + fc.xm * (e[ixm] - ei) + fc.yp * (e[iyp] - ei) + fc.ym * (e[iym] - ei) +
-                     fc.zp * (e[izp] - ei) + fc.zm * (e[izm] - ei);
-        const T r = L0.b[i] - Ae;
+        T r = T(0);
+        if (!zero_black || red) {
+          const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
+          const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
+          const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
+          const Faces<T> fc = faces(L0, i, ixp, ixm, iyp, iym, izp, izm);
+          const T Ae = fc.xp * (e[ixp] - ei) + fc.xm * (e[ixm] - ei) + fc.yp * (e[iyp] - ei) +
+                       fc.ym * (e[iym] - ei) + fc.zp * (e[izp] - ei) + fc.zm * (e[izm] - ei);
+          r = L0.b[i] - Ae;
+        }
         L0.b[i] = r;
         sr.add(r * r);
         const DF s = df_add(DF{a.phi_hi[i], a.phi_lo[i]}, DF{float(ei), 0.f});
