@@ -46,6 +46,20 @@ __device__ __forceinline__ void box_site(const Dims &d, const Box &b, long long 
   z = ((b.lo[2] + int(t / ((long long)b.cnt[0] * b.cnt[1]))) % d.nz + d.nz) % d.nz;
 }
 
+// Position of a node or sample relative to the sphere centre, split into
+// the integer part of the centre (exact) and a fractional remainder: in FP32
+// the offset d = (x - floor(X)) + o - frac(X) is then within 1e-6 of the exact
+// value times 2^-23 |d|, so |d^2 - r^2| > 1e-3 + 1e-5 r^2 decides "inside"
+// exactly as the rounded FP64 test does; closer cases use the FP64 test itself.
+constexpr float kCertain = 1e-3f;
+
+__device__ __forceinline__ int wrap_rel(int dx, int n) {
+  // minimum-image integer offset in (-n/2, n/2]
+  if (dx > n / 2) dx -= n;
+  if (dx <= -((n + 1) / 2)) dx += n;
+  return dx;
+}
+
 template <typename T>
 __global__ void k_project(Dims d, int h, const double *__restrict__ cx, const double *__restrict__ cr,
                           uint8_t *__restrict__ solid, int *__restrict__ owner, T *__restrict__ psi_s) {
@@ -53,43 +67,76 @@ __global__ void k_project(Dims d, int h, const double *__restrict__ cx, const do
   const double X[3] = {cx[3 * j], cx[3 * j + 1], cx[3 * j + 2]};
   const double r = cr[j];
   const double r2 = __dmul_rn(r, r);
+  const float r2f = float(r2);
+  const float certain = kCertain + 1e-5f * r2f;
   const Box b = bbox(d, X, r, 1.0);
   const long long tot = (long long)b.cnt[0] * b.cnt[1] * b.cnt[2];
   const int hp = h + 1;
   const double inv = double(hp) * hp * hp;
+  const int dims[3] = {d.nx, d.ny, d.nz};
+  int Xi[3];
+  float Xf[3];
+  for (int a = 0; a < 3; ++a) {
+    const double fl = floor(X[a]);
+    Xi[a] = int(fl);
+    Xf[a] = float(X[a] - fl);  // exact difference, rounded once to FP32
+  }
   // sub-cube centre offsets (k + 1/2)/(h+1) - 1/2, once per block
   __shared__ double off[16];
-  if (threadIdx.x < hp) off[threadIdx.x] = __dsub_rn(__ddiv_rn(threadIdx.x + 0.5, double(hp)), 0.5);
+  __shared__ float offf[16];
+  if (threadIdx.x < hp) {
+    off[threadIdx.x] = __dsub_rn(__ddiv_rn(threadIdx.x + 0.5, double(hp)), 0.5);
+    offf[threadIdx.x] = float(off[threadIdx.x]);  // dyadic: exact in FP32
+  }
   __syncthreads();
-  // Every sub-cube centre lies within sqrt(3)/2 < 0.87 of the node.  A node
-  // farther than that margin (plus a relative 1e-9, far above the rounding
-  // of the squared distances) from the sphere surface has all its samples on
-  // one side, so the count is (h+1)^3 or 0 without sampling: the same count
-  // the rounded per-sample test gives.
-  // (used only where every sample and the node share one periodic image)
-  const double r_in = r - 0.87 - 1e-9 * r, r_out = r + 0.87 + 1e-9 * r;
+  // Every sub-cube centre lies within sqrt(3) (1/2 - 1/(2(h+1))) of its node;
+  // a node farther than that (plus 1e-3) from the sphere surface has all its
+  // samples on one side.  Used only where every sample and the node share one
+  // periodic image.
+  const double reach = 1.7320508075688772 * (0.5 - 0.5 / double(hp)) + 1e-3;
+  const double r_in = r - reach, r_out = r + reach;
   const bool shortcut = 2.0 * (r_out + 1.0) < double(min(d.nx, min(d.ny, d.nz)));
   for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
     int x, y, z;
     box_site(d, b, t, x, y, z);
     const long long i = site(d, x, y, z);
-    const double d2 = dist2(double(x), double(y), double(z), X, d);
-    if (d2 < r2) {
+    const int p[3] = {x, y, z};
+    float rel[3];
+    for (int a = 0; a < 3; ++a) rel[a] = float(wrap_rel(p[a] - Xi[a], dims[a])) - Xf[a];
+    const float d2f = rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2];
+    // (the FP32 offsets pick the nearest periodic image; the FP64 test may pick
+    // the other one only for samples about half a box away, which are outside
+    // whenever the shortcut condition holds, so the fast path is used only then)
+    bool in_node;
+    if (shortcut && fabsf(d2f - r2f) > certain) in_node = d2f < r2f;
+    else in_node = dist2(double(x), double(y), double(z), X, d) < r2;
+    if (in_node) {
       solid[i] = 1;
       atomicMax(owner + i, j);
     }
     int nu = 0;
-    if (shortcut && r_in > 0.0 && d2 < r_in * r_in) {
+    const float rinf = float(r_in), routf = float(r_out);
+    if (shortcut && r_in > 0.0 && d2f < rinf * rinf - certain) {
       nu = hp * hp * hp;
-    } else if (shortcut && d2 > r_out * r_out) {
+    } else if (shortcut && d2f > routf * routf + certain) {
       nu = 0;
     } else {
       for (int kz = 0; kz < hp; ++kz) {
-        const double pz = __dadd_rn(double(z), off[kz]);
+        const float qz = rel[2] + offf[kz];
         for (int ky = 0; ky < hp; ++ky) {
-          const double py = __dadd_rn(double(y), off[ky]);
-          for (int kx = 0; kx < hp; ++kx)
-            if (dist2(__dadd_rn(double(x), off[kx]), py, pz, X, d) < r2) ++nu;
+          const float qy = rel[1] + offf[ky];
+          const float s2 = qy * qy + qz * qz;
+          for (int kx = 0; kx < hp; ++kx) {
+            const float qx = rel[0] + offf[kx];
+            const float e2 = qx * qx + s2;
+            bool in;
+            if (shortcut && fabsf(e2 - r2f) > certain)
+              in = e2 < r2f;
+            else
+              in = dist2(__dadd_rn(double(x), off[kx]), __dadd_rn(double(y), off[ky]), __dadd_rn(double(z), off[kz]),
+                         X, d) < r2;
+            nu += in ? 1 : 0;
+          }
         }
       }
     }

@@ -734,26 +734,22 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
       // FP32 modes: r <- r - A e on the FP32 level-0 residual (its rounding error is
       // relative to |A e| ~ |r|), phi += e in double-float; the double-float residual
       // of the first pass fixes the starting point of each solve
-      // after the closing black half sweep the residual of the correction
-      // equation vanishes on black cells; only red cells form r - A e
-      const bool zero_black = L0.rb && a.tail > 0;
       SumAcc<DFM> sr, sp;
       for (long long i = gt; i < N; i += G) {
         int x, y, z;
         coords(d, i, x, y, z);
-        const bool red = !((x + y + z) & 1);
+        const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
+        const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
+        const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
         const T *e = L0.x;
         const T ei = e[i];
-        T r = T(0);
-        if (!zero_black || red) {
-          const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
-          const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
-          const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
-          const Faces<T> fc = faces(L0, i, ixp, ixm, iyp, iym, izp, izm);
-          const T Ae = fc.xp * (e[ixp] - ei) + fc.xm * (e[ixm] - ei) + fc.yp * (e[iyp] - ei) +
-                       fc.ym * (e[iym] - ei) + fc.zp * (e[izp] - ei) + fc.zm * (e[izm] - ei);
-          r = L0.b[i] - Ae;
-        }
+        const Faces<T> fc = faces(L0, i, ixp, ixm, iyp, iym, izp, izm);
+        const T Ae = fc.xp * (e[ixp] - ei) + fc.xm * (e[ixm] - ei) + fc.yp * (e[iyp] - ei) + fc.ym * (e[iym] - ei) +
+                     fc.zp * (e[izp] - ei) + fc.zm * (e[izm] - ei);
+        // every cell, black ones included: after the black half sweep their
+        // residual is zero only up to the FP32 rounding of the update, which
+        // scales with the correction and must stay visible to later cycles
+        const T r = L0.b[i] - Ae;
         L0.b[i] = r;
         sr.add(r * r);
         const DF s = df_add(DF{a.phi_hi[i], a.phi_lo[i]}, DF{float(ei), 0.f});

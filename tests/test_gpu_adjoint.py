@@ -164,6 +164,6 @@ def test_autograd_function_returns_the_adjoint_gradients(lbeh):
     s = factory([0.0, 0.0, 2e-2], 4.0, 5.0)
     g = s.step_adjoint(nsteps, 2, d_deformation=1.0, dn0_dQ=dn)
     s.close()
-    assert float(D) == g["deformation"]
+    assert float(D.detach()) == g["deformation"]
     assert np.allclose(E.grad.numpy(), 3.0 * g["dE_ext"], rtol=0, atol=0)
     assert float(G.grad) == 3.0 * g["dG"] and float(Q.grad) == 3.0 * g["dQ"]
