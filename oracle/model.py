@@ -18,6 +18,12 @@ none explicitly):
      correction and momentum exchange (Sec. II.A, II.E);
   8. moving colloids: forces, velocity-Verlet, remap (Sec. II.E).
 
+Pins: every part above has its own pin (exact moments and symbols, brute
+force, closed forms, conservation); the composed step is checked by exact
+conservation of mass, ions and charge, momentum with moving colloids and the
+O'Konski deformation of a dielectric drop.  Parity unpinned beyond those: no
+worked example of the paper fixes the composed step's values.
+
 Lattice units: dx = dt = e = beta = rho0 = 1.  sigma = 0 is component a
 ("red", water), sigma = 1 is component b ("blue", oil).  Species s = 0 is the
 cation (z = +1), s = 1 the anion (z = -1).

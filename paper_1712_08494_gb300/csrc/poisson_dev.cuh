@@ -426,7 +426,7 @@ __device__ __forceinline__ int ld_acquire_s32(const int *p) {
 // Grid barrier: thread 0 of every block arrives with an acquire-release add
 // on a monotonic counter (releasing the block's writes, ordered by the
 // preceding __syncthreads) and polls it with acquire loads until all blocks of
-// this round have arrived.  The wait is bounded; on time-out the block raises
+// this barrier generation have arrived.  The wait is bounded; on time-out the block raises
 // the abort flag and the status, and every block leaves at its next barrier.
 __device__ __forceinline__ bool grid_sync(Bar *bar, int *status) {
   __shared__ int ok;
