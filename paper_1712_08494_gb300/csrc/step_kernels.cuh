@@ -437,8 +437,10 @@ __device__ __forceinline__ void collide_site(const StepK<T> &k, const S *__restr
   }
 }
 
+// One component keeps about half the live state of two: four resident blocks
+// per SM (64 registers) hide more latency there; two components stay at three.
 template <typename S, typename T, int NC, bool SOL, bool IONS>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, NC == 1 ? 4 : 3)
     k_collide(StepK<T> k, const S *__restrict__ f, S *__restrict__ fn, const T *__restrict__ rhoF,
               const T *__restrict__ JF, const T *__restrict__ psiF, const T *__restrict__ eps,
               const T *__restrict__ phi, const T *__restrict__ n, const T *__restrict__ psi_f,
