@@ -29,7 +29,7 @@ template <typename S, typename T> struct BatchRec {
 };
 
 template <typename S, typename T, int NC, bool IONS, bool DFM>
-__global__ void __launch_bounds__(kPB, 1)
+__global__ void __launch_bounds__(kPB, 2)
     k_batch(const BatchRec<S, T> *__restrict__ recs, int *__restrict__ par, int rec0, int nsteps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[kPB];
