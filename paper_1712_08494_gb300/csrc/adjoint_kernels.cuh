@@ -101,7 +101,7 @@ __device__ __forceinline__ void block_partials(double v[kAdjPar], double *out) {
 
 // ------------------------------------------------------------------ ak_a
 template <typename T, bool IONS>
-__global__ void __launch_bounds__(256) ak_a(AdjK<T> k, AdjBufs<T> B, double *part) {
+__global__ void __launch_bounds__(256, 2) ak_a(AdjK<T> k, AdjBufs<T> B, double *part) {
   const Dims d = k.d;
   const long long N = d.N;
   double acc[kAdjPar] = {0, 0, 0, 0};
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(256) ak_b(AdjK<T> k, AdjBufs<T> B) {
 
 // ------------------------------------------------------------------ ak_c
 template <typename T, bool IONS>
-__global__ void __launch_bounds__(256) ak_c(AdjK<T> k, AdjBufs<T> B, double *part) {
+__global__ void __launch_bounds__(256, 2) ak_c(AdjK<T> k, AdjBufs<T> B, double *part) {
   const Dims d = k.d;
   const long long N = d.N;
   double acc[kAdjPar] = {0, 0, 0, 0};
