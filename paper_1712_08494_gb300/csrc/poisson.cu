@@ -397,7 +397,9 @@ template <typename T> static bool setup(Poisson *p, const Dims &d) {
   L.push_back(l0);
   while ((int)L.size() < kMaxLevels) {
     const Level<T> &f = L.back();
-    int cf[3] = {f.nx % 2 == 0 && f.nx >= 4, f.ny % 2 == 0 && f.ny >= 4, f.nz % 2 == 0 && f.nz >= 4};
+    // an even axis halves; a two-cell axis coarsens to one cell (no coupling
+    // left along it), which keeps thin boxes' coarse operators isotropic
+    int cf[3] = {f.nx % 2 == 0, f.ny % 2 == 0, f.nz % 2 == 0};
     if (!(cf[0] || cf[1] || cf[2]) || f.N <= 64) break;
     Level<T> c;
     c.nx = cf[0] ? f.nx / 2 : f.nx;
@@ -414,7 +416,8 @@ template <typename T> static bool setup(Poisson *p, const Dims &d) {
     for (int a = 0; a < 3; ++a)
       if (!(l.k[a] = alloc<T>(p, l.N))) return false;
     if (!(l.x = alloc<T>(p, l.N)) || !(l.x2 = alloc<T>(p, l.N)) || !(l.b = alloc<T>(p, l.N))) return false;
-    l.rb = (l.nx % 2 == 0) && (l.ny % 2 == 0) && (l.nz % 2 == 0);
+    l.rb = (l.nx % 2 == 0 || l.nx == 1) && (l.ny % 2 == 0 || l.ny == 1) && (l.nz % 2 == 0 || l.nz == 1) &&
+           l.N % 2 == 0;
   }
   if (cudaFuncSetAttribute(k_tail<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmem) != cudaSuccess)
     return false;

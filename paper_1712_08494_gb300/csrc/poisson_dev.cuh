@@ -52,6 +52,10 @@ __device__ __forceinline__ Faces<T> faces(const Level<T> &L, long long i, long l
     f.zp = L.k[2][i];
     f.zm = L.k[2][izm];
   }
+  // an axis coarsened to a single cell carries no coupling
+  if (L.nx == 1) f.xp = f.xm = T(0);
+  if (L.ny == 1) f.yp = f.ym = T(0);
+  if (L.nz == 1) f.zp = f.zm = T(0);
   return f;
 }
 
@@ -151,18 +155,38 @@ __device__ __forceinline__ void stencil(const Dims &d, const Level<T> &L, long l
   diag = L.h[0] * (kxp + kxm) + L.h[1] * (kyp + kym) + L.h[2] * (kzp + kzm);
 }
 
+// Cell t (< N/2) of one colour, colour = (x + y + z) & 1.  Red-black levels
+// have every extent even or equal to one; cells pair up along the first axis
+// of even extent.
+__device__ __forceinline__ long long rb_cell(const Dims &d, int color, long long t, int &x, int &y, int &z) {
+  if ((d.nx & 1) == 0) {
+    const unsigned hx = unsigned(d.nx / 2);
+    const unsigned r = unsigned(t) / hx;
+    const int xh = int(unsigned(t) - r * hx);
+    z = int(r / unsigned(d.ny));
+    y = int(r - unsigned(z) * unsigned(d.ny));
+    x = 2 * xh + ((y + z + color) & 1);
+  } else if ((d.ny & 1) == 0) {  // nx == 1
+    const unsigned hy = unsigned(d.ny / 2);
+    const unsigned r = unsigned(t) / hy;
+    x = 0;
+    z = int(r);
+    y = 2 * int(unsigned(t) - r * hy) + ((z + color) & 1);
+  } else {  // nx == ny == 1
+    x = 0;
+    y = 0;
+    z = 2 * int(t) + (color & 1);
+  }
+  return site(d, x, y, z);
+}
+
 // one colour of a red-black sweep over the thread range t0, t0+dt, ... < N/2
 template <typename T>
 __device__ __forceinline__ void rb_range(const Level<T> &L, int color, long long t0, long long dt) {
   const Dims d = L.dims();
-  const unsigned hx = unsigned(d.nx / 2);
   for (long long t = t0; t < d.N / 2; t += dt) {
-    const unsigned r = unsigned(t) / hx;
-    const int xh = int(unsigned(t) - r * hx);
-    const int z = int(r / unsigned(d.ny));
-    const int y = int(r - unsigned(z) * unsigned(d.ny));
-    const int x = 2 * xh + ((y + z + color) & 1);
-    const long long i = site(d, x, y, z);
+    int x, y, z;
+    const long long i = rb_cell(d, color, t, x, y, z);
     T off, diag;
     stencil(d, L, i, x, y, z, L.x, off, diag);
     L.x[i] = (off - L.b[i]) / diag;
@@ -696,15 +720,10 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
           rb_range(Ll, 0, gt, G);
           if (!tm.sync()) return;
         } else if (l == 0) {
-          const unsigned hx = unsigned(Ll.nx / 2);
           const Dims dl = Ll.dims();
           for (long long t = gt; t < Ll.N / 2; t += G) {
-            const unsigned r = unsigned(t) / hx;
-            const int xh = int(unsigned(t) - r * hx);
-            const int z = int(r / unsigned(Ll.ny));
-            const int y = int(r - unsigned(z) * unsigned(Ll.ny));
-            const int x = 2 * xh + ((y + z) & 1);
-            const long long i = site(dl, x, y, z);
+            int x, y, z;
+            const long long i = rb_cell(dl, 0, t, x, y, z);
             Ll.x[i] = -Ll.b[i] / diag_at(Ll, i, x, y, z);
           }
           if (!tm.sync()) return;
