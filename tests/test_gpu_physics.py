@@ -1,5 +1,5 @@
-"""Physics of the GPU step: the dielectric drop of Sec. III.B in three
-dimensions.
+"""Physics of the GPU step: the dielectric drop of Sec. III.B, in the paper's
+quasi-2D geometry at its own size and in three dimensions.
 
 An ion-free drop of the lower-permittivity fluid (S = eps_in/eps_out = 1/2,
 the ratio of the 128^3 droplet workload) of radius 24 in a 128^3 box, in a
@@ -10,16 +10,19 @@ paper's eq. droplet_deformation).  gamma is the Shan-Chen surface tension at
 G = 4 measured by the oracle (tests/golden/sc_surface_tension.json, written by
 make_sc_surface_tension.py); D is the deformation the library reports.
 
-The paper's own quasi-2D geometry (a box two cells thick) is not used here:
-the multigrid Poisson solver cannot coarsen a two-cell axis, its coarse
-operators become strongly anisotropic and point red-black smoothing converges
-slowly there.
+Quasi-2D (a box two cells thick, square 128 x 128 section, drop radius
+0.25 l = 32, fields below 0.1): the paper's law
+delta = eps_a r chi^2 E^2 / (4 gamma) (eq. droplet_deformation), for which it
+reports excellent agreement at r >= 30 and within 15% for smaller drops; here
+within 15% (measured 1.128 at chi = 1/3, E = 0.08 and 0.895 at chi = 0.9,
+E = 0.05, stationary from 25 000 steps on).
 """
 import copy
 import json
 import math
 import os
 
+import numpy as np
 import pytest
 
 import synth
@@ -27,6 +30,49 @@ import synth
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sc_surface_tension.json")
+
+
+def _deformation_yz(rho, n):
+    ra, rb = rho
+    c = (rb - ra) / (ra + rb)
+    w = np.maximum(c, 0.0).sum(axis=2)
+    z, y = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    W = w.sum()
+    yc, zc = (w * y).sum() / W, (w * z).sum() / W
+    myy, mzz = (w * (y - yc) ** 2).sum(), (w * (z - zc) ** 2).sum()
+    return (math.sqrt(mzz) - math.sqrt(myy)) / (math.sqrt(mzz) + math.sqrt(myy))
+
+
+@pytest.mark.parametrize("eps_b,E", [(0.5, 0.08), (0.05263157894736842, 0.05)])
+def test_dielectric_drop_quasi_2d_at_paper_size(lbeh, eps_b, E):
+    gamma = json.load(open(GOLDEN))["gamma"]
+    n, r = 128, 32.0
+    w = synth.droplet(n=n, r=r, G=4.0, Ez=0.0, nions=0, tol=1e-6, noise=0.0, eps_r=(1.0, eps_b), prec="fp32")
+    w.params.nx = 2
+    w.params.poisson_max_iter = 200
+    rho = w.rho[:, :, :, n // 2 - 1:n // 2 + 1].copy()
+    relax = lbeh.System(w.params)
+    relax.set_fields(rho=list(rho))
+    assert relax.step(10000) == lbeh.LBEH_OK
+    f = relax.get(("rho",), f=True)
+    relax.close()
+    ra, rb = f["rho"]
+    rd = math.sqrt(float(((rb - ra) > 0)[:, :, 0].sum()) / math.pi)
+    p = copy.deepcopy(w.params)
+    p.E_ext = (0.0, 0.0, E)
+    s = lbeh.System(p)
+    s.set_fields(f=f["f"])
+    assert s.step(20000) == lbeh.LBEH_OK
+    d1 = _deformation_yz(s.get(("rho",))["rho"], n)
+    assert s.step(5000) == lbeh.LBEH_OK
+    d2 = _deformation_yz(s.get(("rho",))["rho"], n)
+    s.close()
+    eps_a = 1.0 / (4.0 * math.pi * 0.4)
+    chi = (1.0 - eps_b) / (1.0 + eps_b)
+    delta_th = eps_a * rd * chi ** 2 * E ** 2 / (4.0 * gamma)
+    assert d2 > 0.0                       # prolate along the field
+    assert abs(d2 - d1) < 0.03 * d2       # stationary
+    assert abs(d2 / delta_th - 1.0) < 0.15, (d2, delta_th, rd)
 
 
 def test_dielectric_drop_3d_small_deformation(lbeh):
