@@ -41,6 +41,12 @@ _FIELDS = (2 + 3 + 2 + 1 + 1 + 2) * 4 + (3 + 6) * 4
 COLLIDE_BYTES = {"fp32": 2 * 19 * 4 * 2 + _FIELDS, "bf16": 2 * 19 * 2 * 2 + _FIELDS}
 
 
+# Poisson solve: 16 B/site per fine-level sweep (potential read and written,
+# eps and q read), V(NU_SMOOTH, NU_SMOOTH) cycles
+POISSON_BYTES_PER_SWEEP = 16
+NU_SMOOTH = 2
+
+
 def collide_bytes(ncomp, pop_bytes, solids):
     """Algorithmic bytes per site of k_collide with ions and a field: populations
     read + written, rho (ncomp), J (3), psi (two components only), eps, phi,
@@ -173,6 +179,31 @@ def ncu_traffic(prec):
         return None
     m = re.search(r"traffic_%s_bytes_per_launch:\s*([0-9.eE+]+)" % prec, txt)
     return float(m.group(1)) if m else None
+
+
+def poisson_source_hash():
+    h = hashlib.sha256()
+    for f in ("poisson_dev.cuh", "poisson.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1712_08494_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_poisson_traffic(cycles_per_solve):
+    """DRAM bytes per k_poisson launch from the committed ncu summary when it
+    was taken on the current solver source: the captured launch's bytes per
+    multigrid cycle times the cycles of an average solve (else None)."""
+    p = os.path.join(ROOT, "profiles", "k_poisson_droplet128.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != poisson_source_hash():
+        return None
+    b = re.search(r"traffic_fp32_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    c = re.search(r"cycles_of_captured_launch:\s*([0-9.eE+]+)", txt)
+    if not b or not c:
+        return None
+    return float(b.group(1)) / float(c.group(1)) * cycles_per_solve
 
 
 def cpu_baseline(n, budget_s=30.0):
@@ -328,6 +359,16 @@ def run_ours(args):
     t_collb = profb["ms"]["collide"] / max(1, profb["calls"]["collide"]) * 1e-3
     achievedb = COLLIDE_BYTES["bf16"] * N / t_collb / 1e9
     tr = ncu_traffic("fp32")
+    # k_poisson, the kernel with the largest share of the step: one launch is
+    # one solve; algorithmic bytes = 16 B/site per fine-level sweep (potential
+    # read and written, eps, q) times the 2 * NU_SMOOTH fine sweeps of each
+    # V(NU, NU) multigrid cycle
+    calls_p = max(1, prof["calls"]["poisson"])
+    t_pois = prof["ms"]["poisson"] / calls_p * 1e-3
+    cyc_solve = prof["poisson_cycles"] / calls_p
+    pois_bytes = POISSON_BYTES_PER_SWEEP * 2 * NU_SMOOTH * cyc_solve * N
+    achieved_p = pois_bytes / t_pois / 1e9 if t_pois > 0 else 0.0
+    tr_p = ncu_poisson_traffic(cyc_solve)
 
     if rank != 0:
         return
@@ -353,10 +394,15 @@ def run_ours(args):
                          "deformation_bf16": results["bf16"]["obs"].deformation,
                          "ms_per_step": msbf / args.steps,
                          "collide_gbs": achievedb},
-        "roofline": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": tr,
-                     "algorithmic_bytes_per_launch": COLLIDE_BYTES["fp32"] * N,
-                     "avg_launch_ms": t_coll * 1e3},
+        "roofline": {"bound": "hbm", "kernel": "k_poisson", "achieved": achieved_p, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved_p / peak, "traffic": tr_p,
+                     "algorithmic_bytes_per_launch": pois_bytes, "avg_launch_ms": t_pois * 1e3,
+                     "multigrid_cycles_per_launch": cyc_solve,
+                     "bytes_rule": "16 B/site x 2*%d fine sweeps per V(%d,%d) cycle" % (NU_SMOOTH, NU_SMOOTH, NU_SMOOTH)},
+        "roofline_collide": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
+                             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": tr,
+                             "algorithmic_bytes_per_launch": COLLIDE_BYTES["fp32"] * N,
+                             "avg_launch_ms": t_coll * 1e3},
         "stage_share": {k: (v / total_ms if total_ms else None) for k, v in prof["ms"].items()},
         "poisson_cycles_per_step": results["fp32"]["cycles"] / args.steps,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": prof["launches"],
@@ -390,7 +436,9 @@ def suspension_run(lbeh, stream, peak, peak_kind, args, n=256, steps=100):
         s.set_fields(rho=list(w.rho), n=list(w.n), colloid_x=w.colloid_x, colloid_v=w.colloid_v,
                      colloid_q=w.colloid_q, colloid_r=w.colloid_r)
         s.step(5)
+        s.profile_enable(False)  # resets the launch and cycle counters
         ms, rc = _timed(s.step, stream, steps)
+        cycles = s.profile_read()["poisson_cycles"]
         s.profile_enable(True)
         s.step(min(steps, 50))
         prof = s.profile_read()
@@ -401,6 +449,7 @@ def suspension_run(lbeh, stream, peak, peak_kind, args, n=256, steps=100):
         gbs = collide_bytes(1, 4 if prec == "fp32" else 2, True) * n ** 3 / t_coll / 1e9
         total = sum(prof["ms"].values())
         out[prec] = {"mlups": n ** 3 * steps / (ms * 1e3), "ms_per_step": ms / steps, "status": rc,
+                     "poisson_cycles_per_step": cycles / steps,
                      "collide_gbs": gbs, "collide_frac": gbs / peak, "peak_kind": peak_kind,
                      "stage_share": {k: (v / total if total else None) for k, v in prof["ms"].items()}}
     out["bf16_speedup"] = out["bf16"]["mlups"] / out["fp32"]["mlups"]

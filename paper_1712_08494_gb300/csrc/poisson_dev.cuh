@@ -32,9 +32,8 @@ template <typename T> struct Level {
 template <typename T> struct Faces {
   T xp, xm, yp, ym, zp, zm;
 };
-template <typename T>
-__device__ __forceinline__ Faces<T> faces(const Level<T> &L, long long i, long long ixp, long long ixm, long long iyp,
-                                          long long iym, long long izp, long long izm) {
+template <typename T, typename I>
+__device__ __forceinline__ Faces<T> faces(const Level<T> &L, I i, I ixp, I ixm, I iyp, I iym, I izp, I izm) {
   Faces<T> f;
   if (L.eps) {
     const T e = L.eps[i];
@@ -155,6 +154,113 @@ __device__ __forceinline__ void stencil(const Dims &d, const Level<T> &L, long l
   diag = L.h[0] * (kxp + kxm) + L.h[1] * (kyp + kym) + L.h[2] * (kzp + kzm);
 }
 
+// 32-bit cell walks.  Levels hold fewer than 2^31 cells.  A thread visits the
+// cells t0, t0 + dt, ... of a row-major range of rows of width w (w = nx for
+// every cell of a level, nx/2 for one colour of a red-black level with nx
+// even); its position (u, y, z) advances by the stride decomposed once, with
+// no per-cell division, and the walk ends when z reaches nz.
+struct Walk {
+  int u, y, z, du, dy, dz, w, ny;
+  __device__ __forceinline__ Walk(long long t0, long long dt, int w_, int ny_) : w(w_), ny(ny_) {
+    const unsigned uw = unsigned(w_), uny = unsigned(ny_);
+    unsigned r = unsigned(t0) / uw;
+    u = int(unsigned(t0) - r * uw);
+    y = int(r % uny);
+    z = int(r / uny);
+    r = unsigned(dt) / uw;
+    du = int(unsigned(dt) - r * uw);
+    dy = int(r % uny);
+    dz = int(r / uny);
+  }
+  __device__ __forceinline__ void next() {
+    u += du;
+    int c = u >= w;
+    if (c) u -= w;
+    y += dy + c;
+    c = y >= ny;
+    if (c) y -= ny;
+    z += dz + c;
+  }
+};
+
+__device__ __forceinline__ unsigned site32(const Dims &d, int x, int y, int z) {
+  return (unsigned(z) * unsigned(d.ny) + unsigned(y)) * unsigned(d.nx) + unsigned(x);
+}
+
+// Passes over levels of at least kPfCells cells stream arrays larger than the
+// L2; there each thread asks the L2 for the cell kPf iterations ahead of the
+// one it works on (prefetch.global.L2 is a hint: it loads nothing into
+// registers), which keeps more DRAM requests in flight than the 32 resident
+// warps per SM issue on their own.  Smaller levels stay in the L2, where the
+// hints would only cost instructions.
+constexpr int kPf = 4;
+constexpr long long kPfCells = 1LL << 22;
+__device__ __forceinline__ void pf_l2(const void *p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
+// cell (x, y, z) and its six periodic neighbours as 32-bit indices
+struct Nbr {
+  unsigned i, xp, xm, yp, ym, zp, zm;
+};
+__device__ __forceinline__ Nbr nbr(const Dims &d, int x, int y, int z) {
+  const unsigned nx = unsigned(d.nx), sz = nx * unsigned(d.ny), n = unsigned(d.N);
+  Nbr c;
+  c.i = site32(d, x, y, z);
+  c.xp = x + 1 == d.nx ? c.i - (nx - 1) : c.i + 1;
+  c.xm = x == 0 ? c.i + (nx - 1) : c.i - 1;
+  c.yp = y + 1 == d.ny ? c.i - (sz - nx) : c.i + nx;
+  c.ym = y == 0 ? c.i + (sz - nx) : c.i - nx;
+  c.zp = z + 1 == d.nz ? c.i - (n - sz) : c.i + sz;
+  c.zm = z == 0 ? c.i + (n - sz) : c.i - sz;
+  return c;
+}
+
+// the level stencil at a cell given by its neighbour indices: the same
+// arithmetic as stencil()
+template <typename T>
+__device__ __forceinline__ void stencil_n(const Level<T> &L, const Nbr &c, const T *__restrict__ xv, T &off,
+                                          T &diag) {
+  const Faces<T> f = faces(L, c.i, c.xp, c.xm, c.yp, c.ym, c.zp, c.zm);
+  const T kxp = f.xp, kxm = f.xm, kyp = f.yp, kym = f.ym, kzp = f.zp, kzm = f.zm;
+  off = L.h[0] * (kxp * xv[c.xp] + kxm * xv[c.xm]) + L.h[1] * (kyp * xv[c.yp] + kym * xv[c.ym]) +
+        L.h[2] * (kzp * xv[c.zp] + kzm * xv[c.zm]);
+  diag = L.h[0] * (kxp + kxm) + L.h[1] * (kyp + kym) + L.h[2] * (kzp + kzm);
+}
+template <typename T> __device__ __forceinline__ T diag_n(const Level<T> &L, const Nbr &c) {
+  const Faces<T> f = faces(L, c.i, c.xp, c.xm, c.yp, c.ym, c.zp, c.zm);
+  return L.h[0] * (f.xp + f.xm) + L.h[1] * (f.yp + f.ym) + L.h[2] * (f.zp + f.zm);
+}
+
+// Coarse face coefficient along axis AX of coarse cell (X, Y, Z): the mean of
+// the fine face coefficients on that face (fine cells of the coarse cell's
+// block next to its +AX face).  Axis indices are compile-time constants, so
+// the small coordinate arrays stay in registers.
+template <int AX, typename T>
+__device__ __forceinline__ T coarse_coef(const Level<T> &F, const Level<T> &C, int X, int Y, int Z) {
+  constexpr int B1 = (AX + 1) % 3, B2 = (AX + 2) % 3;
+  const Dims f = F.dims();
+  const int fn[3] = {f.nx, f.ny, f.nz};
+  int p[3] = {C.cf[0] ? 2 * X : X, C.cf[1] ? 2 * Y : Y, C.cf[2] ? 2 * Z : Z};
+  if (C.cf[AX]) p[AX] += 1;
+  T acc = T(0);
+  int cnt = 0;
+  for (int t1 = 0; t1 <= C.cf[B1]; ++t1)
+    for (int t2 = 0; t2 <= C.cf[B2]; ++t2) {
+      int q[3] = {p[0], p[1], p[2]};
+      q[B1] += t1;
+      q[B2] += t2;
+      const unsigned fi = site32(f, q[0], q[1], q[2]);
+      if (F.eps) {
+        int r[3] = {q[0], q[1], q[2]};
+        r[AX] = r[AX] + 1 == fn[AX] ? 0 : r[AX] + 1;
+        acc += T(0.5) * (F.eps[fi] + F.eps[site32(f, r[0], r[1], r[2])]);
+      } else {
+        acc += F.k[AX][fi];
+      }
+      ++cnt;
+    }
+  return acc / T(cnt);
+}
+
 // Cell t (< N/2) of one colour, colour = (x + y + z) & 1.  Red-black levels
 // have every extent even or equal to one; cells pair up along the first axis
 // of even extent.
@@ -184,6 +290,23 @@ __device__ __forceinline__ long long rb_cell(const Dims &d, int color, long long
 template <typename T>
 __device__ __forceinline__ void rb_range(const Level<T> &L, int color, long long t0, long long dt) {
   const Dims d = L.dims();
+  if ((d.nx & 1) == 0) {  // pairs along x: the walk of rb_cell without divisions
+    const bool pf = kPf && d.N >= kPfCells;
+    Walk wp(t0 + kPf * dt, dt, d.nx / 2, d.ny);
+    for (Walk w(t0, dt, d.nx / 2, d.ny); w.z < d.nz; w.next(), wp.next()) {
+      if (pf && wp.z < d.nz) {
+        const unsigned ip = site32(d, 2 * wp.u + ((wp.y + wp.z + color) & 1), wp.y, wp.z);
+        pf_l2(L.x + ip);
+        pf_l2(L.b + ip);
+        if (L.eps) pf_l2(L.eps + ip);
+      }
+      const Nbr c = nbr(d, 2 * w.u + ((w.y + w.z + color) & 1), w.y, w.z);
+      T off, diag;
+      stencil_n(L, c, L.x, off, diag);
+      L.x[c.i] = (off - L.b[c.i]) / diag;
+    }
+    return;
+  }
   for (long long t = t0; t < d.N / 2; t += dt) {
     int x, y, z;
     const long long i = rb_cell(d, color, t, x, y, z);
@@ -222,9 +345,8 @@ template <typename T> __device__ __forceinline__ T diag_at(const Level<T> &L, lo
 template <typename T>
 __device__ __forceinline__ void restrict_range(const Level<T> &F, const Level<T> &C, long long t0, long long dt) {
   const Dims f = F.dims(), c = C.dims();
-  for (long long I = t0; I < c.N; I += dt) {
-    int X, Y, Z;
-    coords(c, I, X, Y, Z);
+  for (Walk w(t0, dt, c.nx, c.ny); w.z < c.nz; w.next()) {
+    const int X = w.u, Y = w.y, Z = w.z;
     T acc = T(0);
     int cnt = 0;
     for (int tz = 0; tz <= C.cf[2]; ++tz)
@@ -233,14 +355,15 @@ __device__ __forceinline__ void restrict_range(const Level<T> &F, const Level<T>
           const int x = C.cf[0] ? 2 * X + tx : X, y = C.cf[1] ? 2 * Y + ty : Y, z = C.cf[2] ? 2 * Z + tz : Z;
           ++cnt;
           if (F.rb && ((x + y + z) & 1)) continue;
-          const long long i = site(f, x, y, z);
+          const Nbr n = nbr(f, x, y, z);
           T off, diag;
-          stencil(f, F, i, x, y, z, F.x, off, diag);
-          acc += F.b[i] - (off - diag * F.x[i]);
+          stencil_n(F, n, F.x, off, diag);
+          acc += F.b[n.i] - (off - diag * F.x[n.i]);
         }
     const T bI = acc / T(cnt);
-    C.b[I] = bI;
-    if (C.rb && !((X + Y + Z) & 1)) C.x[I] = -bI / diag_at(C, I, X, Y, Z);
+    const Nbr nc = nbr(c, X, Y, Z);
+    C.b[nc.i] = bI;
+    if (C.rb && !((X + Y + Z) & 1)) C.x[nc.i] = -bI / diag_n(C, nc);
   }
 }
 
@@ -251,18 +374,25 @@ __device__ __forceinline__ void prolong_range(const Level<T> &F, const Level<T> 
   const int cd[3] = {c.nx, c.ny, c.nz};
   if (C.cf[0] && C.cf[1] && C.cf[2]) {
     // coarsened along every axis: weights 27/64, 9/64, 3/64, 1/64
-    for (long long i = t0; i < f.N; i += dt) {
-      int x, y, z;
-      coords(f, i, x, y, z);
+    const unsigned cnx = unsigned(c.nx), cny = unsigned(c.ny), fnx = unsigned(f.nx), fny = unsigned(f.ny);
+    const bool pf = kPf && f.N >= kPfCells;
+    Walk wp(t0 + kPf * dt, dt, f.nx, f.ny);
+    for (Walk w(t0, dt, f.nx, f.ny); w.z < f.nz; w.next(), wp.next()) {
+      if (pf && wp.z < f.nz) pf_l2(F.x + site32(f, wp.u, wp.y, wp.z));
+      const int x = w.u, y = w.y, z = w.z;
+      const unsigned i = (unsigned(z) * fny + unsigned(y)) * fnx + unsigned(x);
       const int X0 = x >> 1, Y0 = y >> 1, Z0 = z >> 1;
       const int X1 = (x & 1) ? (X0 + 1 == c.nx ? 0 : X0 + 1) : (X0 == 0 ? c.nx - 1 : X0 - 1);
       const int Y1 = (y & 1) ? (Y0 + 1 == c.ny ? 0 : Y0 + 1) : (Y0 == 0 ? c.ny - 1 : Y0 - 1);
       const int Z1 = (z & 1) ? (Z0 + 1 == c.nz ? 0 : Z0 + 1) : (Z0 == 0 ? c.nz - 1 : Z0 - 1);
+      // coarse row starts of the four (Y, Z) combinations
+      const unsigned r00 = (unsigned(Z0) * cny + unsigned(Y0)) * cnx, r10 = (unsigned(Z0) * cny + unsigned(Y1)) * cnx;
+      const unsigned r01 = (unsigned(Z1) * cny + unsigned(Y0)) * cnx, r11 = (unsigned(Z1) * cny + unsigned(Y1)) * cnx;
       const T *cx = C.x;
-      const T v000 = cx[site(c, X0, Y0, Z0)];
-      const T v100 = cx[site(c, X1, Y0, Z0)], v010 = cx[site(c, X0, Y1, Z0)], v001 = cx[site(c, X0, Y0, Z1)];
-      const T v110 = cx[site(c, X1, Y1, Z0)], v101 = cx[site(c, X1, Y0, Z1)], v011 = cx[site(c, X0, Y1, Z1)];
-      const T v111 = cx[site(c, X1, Y1, Z1)];
+      const T v000 = cx[r00 + X0];
+      const T v100 = cx[r00 + X1], v010 = cx[r10 + X0], v001 = cx[r01 + X0];
+      const T v110 = cx[r10 + X1], v101 = cx[r01 + X1], v011 = cx[r11 + X0];
+      const T v111 = cx[r11 + X1];
       F.x[i] += T(0.421875) * v000 + T(0.140625) * ((v100 + v010) + v001) + T(0.046875) * ((v110 + v101) + v011) +
                 T(0.015625) * v111;
     }
@@ -359,14 +489,14 @@ __device__ void tail_vcycle(const Level<T> *__restrict__ lv, int n, int first, u
     const Level<T> G = lv[l];
     const Level<T> S = sl[l];
     const Dims dg = G.dims();
-    for (long long i = threadIdx.x; i < G.N; i += blockDim.x) {
+    for (Walk w(threadIdx.x, blockDim.x, dg.nx, dg.ny); w.z < dg.nz; w.next()) {
+      const Nbr c = nbr(dg, w.u, w.y, w.z);
+      const unsigned i = c.i;
       if (G.eps) {
-        int x, y, z;
-        coords(dg, i, x, y, z);
         const T e = G.eps[i];
-        S.k[0][i] = T(0.5) * (e + G.eps[site(dg, wrapp(x, dg.nx), y, z)]);
-        S.k[1][i] = T(0.5) * (e + G.eps[site(dg, x, wrapp(y, dg.ny), z)]);
-        S.k[2][i] = T(0.5) * (e + G.eps[site(dg, x, y, wrapp(z, dg.nz))]);
+        S.k[0][i] = T(0.5) * (e + G.eps[c.xp]);
+        S.k[1][i] = T(0.5) * (e + G.eps[c.yp]);
+        S.k[2][i] = T(0.5) * (e + G.eps[c.zp]);
       } else {
         for (int a = 0; a < 3; ++a) S.k[a][i] = G.k[a][i];
       }
@@ -393,7 +523,7 @@ __device__ void tail_vcycle(const Level<T> *__restrict__ lv, int n, int first, u
         L.x[i] = T(0);
       }
       __syncthreads();
-      tail_smooth(L, L.rb ? 10 : 30);
+      tail_smooth(L, L.rb ? 4 : 30);
     } else {
       for (long long i = threadIdx.x; i < L.N; i += blockDim.x) L.x[i] = T(0);
       __syncthreads();
@@ -541,14 +671,11 @@ __device__ __forceinline__ double sum_partials(const double *part, int nb, doubl
 }
 
 template <typename T, bool DFM>
-__device__ __forceinline__ void residual_site(const PArgs<T> &a, const Level<T> &L0, long long i, double qbar,
-                                              DF qbar_df, SumAcc<DFM> &ar, SumAcc<DFM> &ab, SumAcc<DFM> &ap) {
-  const Dims d = L0.dims();
-  int x, y, z;
-  coords(d, i, x, y, z);
-  const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
-  const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
-  const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
+__device__ __forceinline__ void residual_site(const PArgs<T> &a, const Level<T> &L0, int x, int y, int z,
+                                              double qbar, DF qbar_df, SumAcc<DFM> &ar, SumAcc<DFM> &ab,
+                                              SumAcc<DFM> &ap) {
+  const Nbr c = nbr(L0.dims(), x, y, z);
+  const unsigned i = c.i, ixp = c.xp, ixm = c.xm, iyp = c.yp, iym = c.ym, izp = c.zp, izm = c.zm;
   const Faces<T> fc = faces(L0, i, ixp, ixm, iyp, iym, izp, izm);
   const T kxp = fc.xp, kxm = fc.xm, kyp = fc.yp, kym = fc.ym, kzp = fc.zp, kzm = fc.zm;
   if constexpr (DFM) {
@@ -593,7 +720,23 @@ __device__ bool residual_pass(const PArgs<T> &a, const Team &tm, const Level<T> 
                               double *sh, double &r2, double &b2, double &ps) {
   const long long G = tm.size();
   SumAcc<DFM> sr, sb, sp;
-  for (long long i = tm.rank(); i < L0.N; i += G) residual_site<T, DFM>(a, L0, i, qbar, qbar_df, sr, sb, sp);
+  const Dims d = L0.dims();
+  const bool pf = kPf && d.N >= kPfCells;
+  Walk wp(tm.rank() + kPf * G, G, L0.nx, L0.ny);
+  for (Walk w(tm.rank(), G, L0.nx, L0.ny); w.z < L0.nz; w.next(), wp.next()) {
+    if (pf && wp.z < d.nz) {
+      const unsigned ip = site32(d, wp.u, wp.y, wp.z);
+      if (L0.eps) pf_l2(L0.eps + ip);
+      pf_l2(a.q + ip);
+      if constexpr (DFM) {
+        pf_l2(a.phi_hi + ip);
+        pf_l2(a.phi_lo + ip);
+      } else {
+        pf_l2(a.phi + ip);
+      }
+    }
+    residual_site<T, DFM>(a, L0, w.u, w.y, w.z, qbar, qbar_df, sr, sb, sp);
+  }
   const double ar = block_sum_n(sr.get(), sh);
   const double ab = block_sum_n(sb.get(), sh);
   const double ap = block_sum_n(sp.get(), sh);
@@ -661,33 +804,11 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
   for (int l = 1; l < a.nlev; ++l) {
     const Level<T> F = a.lv[l - 1], C = a.lv[l];
     const Dims f = F.dims(), c = C.dims();
-    for (long long I = gt; I < c.N; I += G) {
-      int X, Y, Z;
-      coords(c, I, X, Y, Z);
-      const int base[3] = {C.cf[0] ? 2 * X : X, C.cf[1] ? 2 * Y : Y, C.cf[2] ? 2 * Z : Z};
-      for (int ax = 0; ax < 3; ++ax) {
-        T acc = T(0);
-        int cnt = 0;
-        const int ra = C.cf[ax] ? 1 : 0;
-        const int b1 = (ax + 1) % 3, b2 = (ax + 2) % 3;
-        for (int t1 = 0; t1 <= C.cf[b1]; ++t1)
-          for (int t2 = 0; t2 <= C.cf[b2]; ++t2) {
-            int pp[3];
-            pp[ax] = base[ax] + ra;
-            pp[b1] = base[b1] + t1;
-            pp[b2] = base[b2] + t2;
-            const long long fi = site(f, pp[0], pp[1], pp[2]);
-            if (F.eps) {
-              int q[3] = {pp[0], pp[1], pp[2]};
-              q[ax] = q[ax] + 1 == (ax == 0 ? f.nx : ax == 1 ? f.ny : f.nz) ? 0 : q[ax] + 1;
-              acc += T(0.5) * (F.eps[fi] + F.eps[site(f, q[0], q[1], q[2])]);
-            } else {
-              acc += F.k[ax][fi];
-            }
-            ++cnt;
-          }
-        C.k[ax][I] = acc / T(cnt);
-      }
+    for (Walk w(gt, G, c.nx, c.ny); w.z < c.nz; w.next()) {
+      const unsigned I = site32(c, w.u, w.y, w.z);
+      C.k[0][I] = coarse_coef<0>(F, C, w.u, w.y, w.z);
+      C.k[1][I] = coarse_coef<1>(F, C, w.u, w.y, w.z);
+      C.k[2][I] = coarse_coef<2>(F, C, w.u, w.y, w.z);
     }
     if (!tm.sync()) return;
   }
@@ -721,10 +842,24 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
           if (!tm.sync()) return;
         } else if (l == 0) {
           const Dims dl = Ll.dims();
-          for (long long t = gt; t < Ll.N / 2; t += G) {
-            int x, y, z;
-            const long long i = rb_cell(dl, 0, t, x, y, z);
-            Ll.x[i] = -Ll.b[i] / diag_at(Ll, i, x, y, z);
+          if ((dl.nx & 1) == 0) {
+            const bool pf = kPf && dl.N >= kPfCells;
+            Walk wp(gt + kPf * G, G, dl.nx / 2, dl.ny);
+            for (Walk w(gt, G, dl.nx / 2, dl.ny); w.z < dl.nz; w.next(), wp.next()) {
+              if (pf && wp.z < dl.nz) {
+                const unsigned ip = site32(dl, 2 * wp.u + ((wp.y + wp.z) & 1), wp.y, wp.z);
+                pf_l2(Ll.b + ip);
+                if (Ll.eps) pf_l2(Ll.eps + ip);
+              }
+              const Nbr c = nbr(dl, 2 * w.u + ((w.y + w.z) & 1), w.y, w.z);
+              Ll.x[c.i] = -Ll.b[c.i] / diag_n(Ll, c);
+            }
+          } else {
+            for (long long t = gt; t < Ll.N / 2; t += G) {
+              int x, y, z;
+              const long long i = rb_cell(dl, 0, t, x, y, z);
+              Ll.x[i] = -Ll.b[i] / diag_at(Ll, i, x, y, z);
+            }
           }
           if (!tm.sync()) return;
         }
@@ -754,12 +889,19 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
       // relative to |A e| ~ |r|), phi += e in double-float; the double-float residual
       // of the first pass fixes the starting point of each solve
       SumAcc<DFM> sr, sp;
-      for (long long i = gt; i < N; i += G) {
-        int x, y, z;
-        coords(d, i, x, y, z);
-        const long long ixp = site(d, wrapp(x, d.nx), y, z), ixm = site(d, wrapm(x, d.nx), y, z);
-        const long long iyp = site(d, x, wrapp(y, d.ny), z), iym = site(d, x, wrapm(y, d.ny), z);
-        const long long izp = site(d, x, y, wrapp(z, d.nz)), izm = site(d, x, y, wrapm(z, d.nz));
+      const bool pf = kPf && d.N >= kPfCells;
+      Walk wp(gt + kPf * G, G, d.nx, d.ny);
+      for (Walk w(gt, G, d.nx, d.ny); w.z < d.nz; w.next(), wp.next()) {
+        if (pf && wp.z < d.nz) {
+          const unsigned ip = site32(d, wp.u, wp.y, wp.z);
+          pf_l2(L0.x + ip);
+          pf_l2(L0.b + ip);
+          if (L0.eps) pf_l2(L0.eps + ip);
+          pf_l2(a.phi_hi + ip);
+          pf_l2(a.phi_lo + ip);
+        }
+        const Nbr c = nbr(d, w.u, w.y, w.z);
+        const unsigned i = c.i, ixp = c.xp, ixm = c.xm, iyp = c.yp, iym = c.ym, izp = c.zp, izm = c.zm;
         const T *e = L0.x;
         const T ei = e[i];
         const Faces<T> fc = faces(L0, i, ixp, ixm, iyp, iym, izp, izm);

@@ -216,6 +216,34 @@ def batch_boxes(nbox=96, seed=3, edges=(32, 40, 48, 56, 64), steps=1000) -> List
     return out
 
 
+def flat_interface(nx=512, ny=4, nz=4, dmu=(2.0, -2.0), chi=0.0, salt=1e-3, G=4.0, drho_a=0.66,
+                   prec="fp32", tol=1e-8, D=0.05, nions=2, rho_major=0.7, rho_minor=0.04) -> Workload:
+    """Quasi-one-dimensional box with two flat fluid interfaces (Sec. III.A):
+    red (fluid a) rho_major/rho_minor (default 0.7/0.04) for x < nx/2,
+    swapped for x >= nx/2, so the
+    periodic box has interfaces near x = nx/2 and x = 0.  Permittivities
+    eps_r = (1, (1 - chi)/(1 + chi)) give the contrast chi = (eps_a - eps_b) /
+    (eps_a + eps_b).  Gibbs transfer energies dmu = (dmu+, dmu-); the initial
+    salt is `salt` in fluid a and salt * exp(-(dmu+ + dmu-)/2) in fluid b, as
+    the paper sets it.  No noise: the state is a function of x only."""
+    shape = (nz, ny, nx)
+    x, y, z = _grid(nx, ny, nz)
+    in_a = x < nx // 2
+    red = np.where(in_a, rho_major, rho_minor)
+    blue = np.where(in_a, rho_minor, rho_major)
+    rho = np.stack([red, blue])
+    ions = None
+    if nions:
+        nb = salt * math.exp(-0.5 * (dmu[0] + dmu[1]))
+        ions = np.stack([np.where(in_a, salt, nb)] * 2).astype(np.float64)
+    p = Params(nx=nx, ny=ny, nz=nz, ncomp=2, nions=nions, prec=prec, tau=1.0, G=G,
+               D=D, bjerrum=0.4, eps_r=(1.0, (1.0 - chi) / (1.0 + chi)), eps_r_colloid=0.125,
+               dmu=tuple(float(v) for v in dmu), drho_a=float(drho_a), E_ext=(0.0, 0.0, 0.0),
+               poisson_tol=tol, poisson_max_iter=200, ncolloid_max=0, rho0_shift=(0.04, 0.04))
+    return Workload("flat_interface_%d" % nx, p, rho, ions, steps=1,
+                    note="flat interfaces, dmu=%s, chi=%g" % (tuple(dmu), chi))
+
+
 def shear_wave(n=32, U=1e-3, rho=1.0, tau=1.0) -> Workload:
     """Single-component, ion-free periodic box whose initial velocity is the
     shear wave u_x(z) = U sin(2 pi z / n) (density uniform)."""
