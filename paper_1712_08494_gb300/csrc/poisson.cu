@@ -400,7 +400,11 @@ template <typename T> static bool setup(Poisson *p, const Dims &d) {
     // an even axis halves; a two-cell axis coarsens to one cell (no coupling
     // left along it), which keeps thin boxes' coarse operators isotropic
     int cf[3] = {f.nx % 2 == 0, f.ny % 2 == 0, f.nz % 2 == 0};
-    if (!(cf[0] || cf[1] || cf[2]) || f.N <= 64) break;
+    // stop at a few cells per axis (4^3 in a cube); thin boxes keep halving
+    // their long axes, whose smooth modes a small coarsest level of many
+    // cells along one axis would barely relax
+    const int ext = std::max(f.nx, std::max(f.ny, f.nz));
+    if (!(cf[0] || cf[1] || cf[2]) || (f.N <= 64 && ext <= 4)) break;
     Level<T> c;
     c.nx = cf[0] ? f.nx / 2 : f.nx;
     c.ny = cf[1] ? f.ny / 2 : f.ny;
