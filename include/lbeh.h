@@ -184,22 +184,24 @@ int lbeh_profile_enable(lbeh_handle *h, int on);
 int lbeh_profile_read(lbeh_handle *h, lbeh_profile *out);
 
 /* Allocation-free observables, for callers that cannot allocate device
- * memory where they need the sums: work recorded inside a stream capture,
- * code under a fixed memory budget, or plugins that only hold borrowed device
- * buffers.  The paper has no counterpart; it is a service entry point of this
- * library.  Inputs are the caller's device buffers: f [ncomp][19][N]
- * populations of element type `dtype` (LBEH_F64 or LBEH_F32, the layout
- * lbeh_get_fields writes with on_device = 1), n [2][N] ions (NULL when
- * nions == 0), solid [N] uint8 mask (NULL: all fluid), qc [N] FP64 colloid
- * charge (NULL: none).  Fills mass, ions, charge, momentum, deformation and
- * centroid of *out exactly as lbeh_observables defines them (other members
- * zero) and synchronises `stream`.  It calls no allocator: its partial sums
- * live in a static device array of LBEH_NOALLOC_SCRATCH_BYTES that every GPU
- * loading the library keeps until exit, which limits N to
- * LBEH_NOALLOC_MAX_SITES (larger boxes: LBEH_ERR_INVALID_ARG).  The first call
- * on a device looks that array up and may initialise the CUDA context: make
- * it outside any stream capture.  All calls share the array; calls whose
- * kernels overlap on the GPU race on it. */
+ * memory where they need the sums: code under a fixed memory budget that
+ * forbids cudaMalloc, plugins that only hold borrowed device buffers, or
+ * processes whose device allocator belongs to another runtime.  The paper has
+ * no counterpart; it is a service entry point of this library.  Inputs are
+ * the caller's device buffers: f [ncomp][19][N] populations of element type
+ * `dtype` (LBEH_F64 or LBEH_F32, the layout lbeh_get_fields writes with
+ * on_device = 1), n [2][N] ions (NULL when nions == 0), solid [N] uint8 mask
+ * (NULL: all fluid), qc [N] FP64 colloid charge (NULL: none).  Fills mass,
+ * ions, charge, momentum, deformation and centroid of *out exactly as
+ * lbeh_observables defines them (other members zero); it ends with a
+ * device-to-host copy of the sums and synchronises `stream`.  It calls no
+ * allocator: its partial sums live in a static device array of
+ * LBEH_NOALLOC_SCRATCH_BYTES that every GPU loading the library keeps until
+ * exit, which limits N to LBEH_NOALLOC_MAX_SITES (larger boxes:
+ * LBEH_ERR_INVALID_ARG, checked before any launch).  The first call in each
+ * CUDA context looks that array's address up in that context (and may
+ * initialise the device's primary context when none is current).  All calls
+ * share the array; calls whose kernels overlap on the GPU race on it. */
 #define LBEH_NOALLOC_MAX_SITES 16777216LL
 #define LBEH_NOALLOC_SCRATCH_BYTES (1024 * 16 * 8 + 16 * 8)
 int lbeh_observables_noalloc(int nx, int ny, int nz, int ncomp, int nions, int dtype, const void *f,

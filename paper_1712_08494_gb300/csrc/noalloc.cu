@@ -1,19 +1,23 @@
 // Allocation-free variant of the observables reduction (lbeh_observables).
 //
 // Some callers cannot allocate device memory at the point where they want
-// the conserved sums: code running inside a stream capture or a memory pool
-// budget that forbids cudaMalloc, plugins that only receive borrowed device
-// buffers, or processes whose allocator is owned by another runtime.  This
-// entry point takes the caller's device fields and a host output struct and
-// allocates nothing: its only scratch (per-block partial sums) lives in the
-// file-scope array below, which every GPU that loads the library holds until
-// the process exits (LBEH_NOALLOC_SCRATCH_BYTES, 128 KiB + 128 B).
+// the conserved sums: code under a memory pool budget that forbids
+// cudaMalloc, plugins that only receive borrowed device buffers, or processes
+// whose allocator is owned by another runtime.  This entry point takes the
+// caller's device fields and a host output struct and allocates nothing: its
+// only scratch (per-block partial sums) lives in the file-scope array below,
+// which every GPU that loads the library holds until the process exits
+// (LBEH_NOALLOC_SCRATCH_BYTES, 128 KiB + 128 B).  It ends with a
+// device-to-host copy of the sums and a synchronisation of the caller's
+// stream.
 //
 // Host code must not pass the array's name to a kernel: on the host it is a
-// stand-in symbol, not a device address.  The first call on each device, with
-// that device current, looks the address up with cudaGetSymbolAddress (which
-// may initialise the CUDA context), caches it per device and passes it to the
-// kernels.  Make that first call outside any stream capture.
+// stand-in symbol, not a device address.  The first call in each CUDA context
+// (the primary context of a device, or a context the caller created and made
+// current) looks the address up with cudaGetSymbolAddress, with that context
+// current, and caches it per context: each context loads its own copy of the
+// module, so an address found in one context is not valid in another.  That
+// first call may initialise the CUDA context.
 //
 // All calls share the array.  Every call overwrites all partials it later
 // reads, so nothing has to start at zero, but two calls whose kernels overlap
@@ -22,6 +26,8 @@
 #include <cstring>
 #include <mutex>
 #include <vector>
+
+#include <cuda.h>
 
 #include "internal.h"
 
@@ -37,20 +43,43 @@ constexpr int kNALen = kObsLen;
 static __device__ __align__(256) double g_obs_scratch[kNAMaxBlocks * kNALen + kNALen];
 
 std::mutex g_mtx;
-std::vector<std::pair<int, double *>> g_addr;  // device ordinal -> scratch address
+std::vector<std::pair<CUcontext, double *>> g_addr;  // CUDA context -> scratch address in it
+
+// cuCtxGetCurrent through the runtime's driver entry point table (no link
+// against the driver library)
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return (CtxGetCurrentFn)f;
+  }();
+  return fn;
+}
 
 int scratch_address(double **out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess) return LBEH_ERR_CUDA;
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get) return LBEH_ERR_CUDA;
+  CUcontext ctx = nullptr;
+  if (get(&ctx) != CUDA_SUCCESS) return LBEH_ERR_CUDA;
   std::lock_guard<std::mutex> lock(g_mtx);
-  for (auto &e : g_addr)
-    if (e.first == dev) {
-      *out = e.second;
-      return LBEH_OK;
-    }
+  if (ctx)
+    for (auto &e : g_addr)
+      if (e.first == ctx) {
+        *out = e.second;
+        return LBEH_OK;
+      }
+  // the lookup runs in the current context; with none current the runtime
+  // initialises the device's primary context and makes it current first
   double *p = nullptr;
   if (cudaGetSymbolAddress((void **)&p, g_obs_scratch) != cudaSuccess || !p) return LBEH_ERR_CUDA;
-  g_addr.emplace_back(dev, p);
+  if (!ctx && (get(&ctx) != CUDA_SUCCESS || !ctx)) return LBEH_ERR_CUDA;
+  g_addr.emplace_back(ctx, p);
   *out = p;
   return LBEH_OK;
 }

@@ -1,8 +1,9 @@
 """Allocation-free observables entry point (lbeh_observables_noalloc).
 
 This variant serves callers that cannot allocate device memory where they
-need the conserved sums (work recorded inside a stream capture, code under a
-fixed memory budget, plugins holding only borrowed device buffers).  It keeps
+need the conserved sums (code under a fixed memory budget, plugins holding
+only borrowed device buffers, processes whose allocator belongs to another
+runtime).  It keeps
 its partial sums in a static device array instead of handle-owned scratch.
 The test feeds it the device copies of a system's fields and checks, on two
 calls in a row, that it reports what lbeh_observables reports for the same
