@@ -27,9 +27,10 @@ where the paper is ambiguous are stated in the docstrings; their list is kept
 with the design notes of the repository.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
-against closed forms, invariants or brute force, except the whole-step
-composition of all couplings at once, whose pin is the set of per-part pins
-plus conservation laws.
+against closed forms, invariants or brute force; the whole-step composition
+of all couplings at once is pinned by a second, site-by-site transcription
+on tiny lattices and by physical laws (Young-Laplace, low-zeta mobility,
+dielectric drop deformation, flat-interface equilibrium).
 """
 
 from .lattice import C, W, OPP, CS2, Q  # noqa: F401

@@ -19,10 +19,12 @@ none explicitly):
   8. moving colloids: forces, velocity-Verlet, remap (Sec. II.E).
 
 Pins: every part above has its own pin (exact moments and symbols, brute
-force, closed forms, conservation); the composed step is checked by exact
-conservation of mass, ions and charge, momentum with moving colloids and the
-O'Konski deformation of a dielectric drop.  Parity unpinned beyond those: no
-worked example of the paper fixes the composed step's values.
+force, closed forms, conservation); the composed step is checked against a
+site-by-site transcription with a dense Poisson solve on tiny lattices, by
+exact conservation of mass, ions and charge, momentum with moving colloids,
+the Young-Laplace law across drop radii, the low-zeta electrophoretic
+mobility and the O'Konski deformation of a dielectric drop.  No worked
+example of the paper fixes the composed step's values.
 
 Lattice units: dx = dt = e = beta = rho0 = 1.  sigma = 0 is component a
 ("red", water), sigma = 1 is component b ("blue", oil).  Species s = 0 is the
