@@ -81,7 +81,24 @@ typedef struct lbeh_params {
   int psi_subdiv;       /* h: solid fraction from (h+1)^3 sub-cube centres (Sec. II.E) */
   int colloids_move;    /* 0: fixed colloids; 1: velocity-Verlet motion and remap */
   void *stream;         /* cudaStream_t all work is issued on (NULL: legacy default stream) */
+  int poisson_solver;   /* LBEH_POISSON_AUTO (0), LBEH_POISSON_MULTIGRID or LBEH_POISSON_SPECTRAL */
 } lbeh_params;
+
+/* Poisson solvers (Sec. II.D).  Both solve the same flux-form equation to
+ * poisson_tol; they differ in cost.  SPECTRAL: conjugate gradients
+ * preconditioned by the constant-coefficient inverse of the seven-point
+ * Laplacian computed with Hartley transforms (the Fourier method of Sec.
+ * II.D); its iteration count grows with the permittivity contrast
+ * eps_max / eps_min.  Each axis must factor into 2, 3, 5 and 7 and be at most
+ * 512 long (256 in FP64), else lbeh_create returns LBEH_ERR_UNSUPPORTED.
+ * MULTIGRID: geometric multigrid defect correction, robust at high contrast
+ * (colloids).  AUTO: spectral for boxes without colloids whose contrast is at
+ * most 4 and whose axes it supports, multigrid otherwise.  poisson_max_iter
+ * counts multigrid cycles or conjugate-gradient iterations.  Batches always
+ * use the multigrid (SPECTRAL there: LBEH_ERR_UNSUPPORTED). */
+#define LBEH_POISSON_AUTO 0
+#define LBEH_POISSON_MULTIGRID 1
+#define LBEH_POISSON_SPECTRAL 2
 
 #define LBEH_F64 0
 #define LBEH_F32 1
@@ -116,9 +133,10 @@ typedef struct lbeh_obs {
   double centroid[3];    /* weighted centre of the drop */
   double colloid_v[3];   /* mean colloid velocity */
   double poisson_relres; /* relative residual of the last solve */
-  int poisson_iters;     /* multigrid cycles of the last solve */
+  int poisson_iters;     /* multigrid cycles or conjugate-gradient iterations of the last solve */
   int status;            /* sticky device status (LBEH_OK or an error code) */
   long long steps;       /* steps taken since the last lbeh_set_fields */
+  int poisson_solver;    /* solver in use: LBEH_POISSON_MULTIGRID or _SPECTRAL (0: no potential) */
 } lbeh_obs;
 
 typedef struct lbeh_handle lbeh_handle;
@@ -162,6 +180,14 @@ int lbeh_observables(lbeh_handle *h, lbeh_obs *out);
 #define LBEH_AUX_RHO_V 7   /* [ncomp][N] densities incl. virtual densities */
 #define LBEH_AUX_U 8       /* [3][N] physical velocity of the last step */
 int lbeh_get_aux(lbeh_handle *h, int which, void *out_host);
+
+/* Time-out of the grid-barrier waits of the one-launch Poisson solves: a
+ * block that polls a barrier `polls` times (about 100 ns each) without every
+ * block arriving raises an abort flag, every block returns, and the step
+ * reports LBEH_ERR_BARRIER_TIMEOUT (sticky until lbeh_set_fields) instead of
+ * hanging.  polls <= 0 restores the default of 2^24 (about two seconds).
+ * Applies to later steps; errors: INVALID_ARG. */
+int lbeh_set_wait_limit(lbeh_handle *h, long long polls);
 
 /* Per-stage device time of lbeh_step, measured with CUDA events recorded on
  * the handle's stream around each stage, and the number of kernels the

@@ -32,6 +32,7 @@ struct Ctx {
   double Eext[3] = {0, 0, 0};
   double shift[2] = {0, 0};
   int h = 3;                // solid-fraction subdivision
+  int psolver = 0;          // Poisson solver: LBEH_POISSON_AUTO, _MULTIGRID or _SPECTRAL
 
   void *f[2] = {nullptr, nullptr};  // populations ping-pong [ncomp][19][N]
   int cur = 0;
@@ -112,7 +113,16 @@ struct PoissonStats {
   int notconv = 0;           // last solve hit the cycle cap
   int body_launches = 0;     // kernels per cycle inside a captured graph
 };
+// Solver of the box: the spectral solve (spectral.cu) when c.psolver asks for
+// it, or, by default, for boxes without colloid capacity whose permittivity contrast
+// is at most kSpectralMaxContrast and whose axes the transforms support; the
+// multigrid otherwise.  Null on failure.
+constexpr double kSpectralMaxContrast = 4.0;
+bool poisson_spectral_choice(const Ctx &c, int fp64);
 Poisson *poisson_create(const Ctx &c, int fp64);
+bool poisson_is_spectral(const Poisson *p);
+// Polls of a grid-barrier wait before the solve gives up (LBEH_ERR_BARRIER_TIMEOUT).
+void poisson_set_wait_limit(Poisson *p, long long polls);
 void poisson_destroy(Poisson *p);
 int poisson_configure(Poisson *p, double tol, int max_iter, cudaStream_t s);
 int poisson_reset(Poisson *p, cudaStream_t s);  // new state: no previous solution to extrapolate from

@@ -54,6 +54,7 @@ struct lbeh_handle {
   lbeh_handle *parent = nullptr;
   bool stats_stale = false;  // Poisson statistics not read back since a batched step
   Poisson *adj_pois = nullptr;  // solver of the adjoint Poisson problems (created on first use)
+  long long wait_limit = 0;     // barrier-wait polls of the Poisson solves (0: default)
 };
 
 std::atomic<long long> lbeh::g_launches{0};
@@ -211,6 +212,7 @@ int check_params(const lbeh_params *p) {
   if (p->nions && (p->dmu[0] != 0.0 || p->dmu[1] != 0.0) && p->drho_a == 0.0) return LBEH_ERR_INVALID_ARG;
   if (p->ncolloid_max < 0 || p->psi_subdiv < 0 || p->psi_subdiv > 15) return LBEH_ERR_INVALID_ARG;
   if (p->poisson_max_iter < 0) return LBEH_ERR_INVALID_ARG;
+  if (p->poisson_solver < LBEH_POISSON_AUTO || p->poisson_solver > LBEH_POISSON_SPECTRAL) return LBEH_ERR_INVALID_ARG;
   return LBEH_OK;
 }
 
@@ -377,6 +379,11 @@ int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
   c.has_field = p->nions > 0 || p->ncolloid_max > 0 || eext;
   c.h = p->psi_subdiv;
   c.ncoll_max = p->ncolloid_max;
+  c.psolver = p->poisson_solver;
+  if (c.has_field && p->poisson_solver == LBEH_POISSON_SPECTRAL && !poisson_spectral_choice(c, p->prec == LBEH_FP64)) {
+    delete h;
+    return LBEH_ERR_UNSUPPORTED;
+  }
   switch (p->prec) {
     case LBEH_FP64: h->ops = ops_f64(); break;
     case LBEH_FP32: h->ops = ops_f32(); break;
@@ -495,9 +502,16 @@ int lbeh_create_batch(const lbeh_params *per_box, int nbox, lbeh_handle **out) {
   h->c.s = (cudaStream_t)per_box[0].stream;
   std::vector<BatchBox> boxes;
   int rc = LBEH_OK;
+  for (int b = 0; b < nbox; ++b)
+    if (per_box[b].poisson_solver == LBEH_POISSON_SPECTRAL) {
+      delete h;
+      return LBEH_ERR_UNSUPPORTED;
+    }
   for (int b = 0; b < nbox && rc == LBEH_OK; ++b) {
     lbeh_handle *bx = nullptr;
-    rc = lbeh_create(&per_box[b], &bx);
+    lbeh_params pb = per_box[b];
+    pb.poisson_solver = LBEH_POISSON_MULTIGRID;  // the batched kernel cycles the multigrid
+    rc = lbeh_create(&pb, &bx);
     if (rc != LBEH_OK) break;
     bx->parent = h;
     h->boxes.push_back(bx);
@@ -538,6 +552,15 @@ int lbeh_batch_tune(lbeh_handle *h, int probe_steps, int *cluster_blocks, double
   for (lbeh_handle *bx : h->boxes)
     if (!bx->loaded) return LBEH_ERR_INVALID_ARG;
   return batch_tune(h->batch, probe_steps, cluster_blocks, ms_per_step);
+}
+
+int lbeh_set_wait_limit(lbeh_handle *h, long long polls) {
+  if (!h || h->batch) return LBEH_ERR_INVALID_ARG;
+  h->wait_limit = polls;
+  if (h->pois) poisson_set_wait_limit(h->pois, polls);
+  if (h->adj_pois) poisson_set_wait_limit(h->adj_pois, polls);
+  drop_graphs(h);  // the captured launches carry the limit by value
+  return LBEH_OK;
 }
 
 int lbeh_profile_enable(lbeh_handle *h, int on) {
@@ -715,10 +738,12 @@ static int batch_advance(lbeh_handle *h, int nsteps, bool sequential) {
     bx->stats_stale = true;
     const int dst = batch_box_status(h->batch, (int)i);
     if (dst & ST_POISSON) bx->status = LBEH_ERR_POISSON_NOT_CONVERGED;
+    if (dst & ST_NONFINITE) bx->status = LBEH_ERR_NONFINITE;
     if (dst & ST_TIMEOUT) bx->status = LBEH_ERR_BARRIER_TIMEOUT;
   }
   h->steps += nsteps;
   if (st & ST_TIMEOUT) return LBEH_ERR_BARRIER_TIMEOUT;
+  if (st & ST_NONFINITE) return LBEH_ERR_NONFINITE;
   if (st & ST_POISSON) return LBEH_ERR_POISSON_NOT_CONVERGED;
   return LBEH_OK;
 }
@@ -767,6 +792,7 @@ int lbeh_step(lbeh_handle *h, int nsteps) {
     int dst = 0;
     cudaMemcpy(&dst, c.status, sizeof(int), cudaMemcpyDeviceToHost);
     if (dst & ST_POISSON) h->status = LBEH_ERR_POISSON_NOT_CONVERGED;
+    if (dst & ST_NONFINITE) h->status = LBEH_ERR_NONFINITE;
     if (dst & ST_TIMEOUT) h->status = LBEH_ERR_BARRIER_TIMEOUT;
   }
   if (cudaPeekAtLastError() != cudaSuccess) return cuda_fail(h, "step");
@@ -827,6 +853,7 @@ int lbeh_observables(lbeh_handle *h, lbeh_obs *out) {
   out->poisson_iters = h->last_iters;
   out->status = h->status;
   out->steps = h->steps;
+  out->poisson_solver = h->pois ? (poisson_is_spectral(h->pois) ? LBEH_POISSON_SPECTRAL : LBEH_POISSON_MULTIGRID) : 0;
   return LBEH_OK;
 }
 
@@ -903,6 +930,7 @@ int lbeh_step_adjoint(lbeh_handle *h, int nsteps, int ckpt_every, const lbeh_obs
     if (!h->adj_pois) {
       h->adj_pois = poisson_create(ca, c.prec == LBEH_FP64);
       if (!h->adj_pois) return LBEH_ERR_OOM;
+      poisson_set_wait_limit(h->adj_pois, h->wait_limit);
     }
     if (poisson_configure(h->adj_pois, h->p.poisson_tol, h->p.poisson_max_iter, c.s) != 0 ||
         poisson_reset(h->adj_pois, c.s) != 0)

@@ -28,6 +28,7 @@
 
 #include "internal.h"
 #include "poisson_dev.cuh"
+#include "spectral_solve.h"
 
 namespace lbeh {
 
@@ -47,6 +48,8 @@ struct Poisson {
   PDev *dev = nullptr;
   std::vector<void *> allocs;
   int body_launches = 0;      // kernels of one cycle (launch accounting in graphs)
+  Spectral *spec = nullptr;   // spectral solve (replaces the multigrid when set)
+  long long spin_limit = kSpinLimit;
 };
 
 // ---------------------------------------------------------------- multi-block kernels
@@ -233,9 +236,10 @@ __global__ void __launch_bounds__(256) k_check(const double *__restrict__ part, 
     st->zero = bn == 0.0;
     const int more = rr >= st->tol && st->iters < st->max_iter;
     st->cond = more;
-    const int fail = rr >= st->tol && st->iters >= st->max_iter;
+    const int fail = (rr >= st->tol && st->iters >= st->max_iter) || !isfinite(rr);
     st->notconv = fail;
     if (fail) atomicOr(status, ST_POISSON);
+    if (!isfinite(rr)) atomicOr(status, ST_NONFINITE);
     if (use_handle) cudaGraphSetConditional(handle, more ? 1u : 0u);
   }
 }
@@ -372,7 +376,7 @@ __global__ void __launch_bounds__(kPB, 2) k_poisson(PArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[kPB];
   __shared__ T sht[kPB];
-  poisson_body<T, DFM>(a, GridTeam{a.bar, a.status}, smem_raw, sh, sht);
+  poisson_body<T, DFM>(a, GridTeam{a.bar, a.status, a.spin_limit}, smem_raw, sh, sht);
 }
 
 // ---------------------------------------------------------------- host
@@ -463,7 +467,7 @@ template <typename T, bool DFM> static PArgs<T> fill_args(Poisson *p, const Ctx 
   PArgs<T> a{};
   a.lv = (const Level<T> *)p->dlevels;
   a.nlev = (int)L.size();
-  a.tail = (int)tail_start(L);
+  a.tail = L.empty() ? 0 : (int)tail_start(L);  // no levels: spectral solve
   a.eps = (const T *)c.eps;
   a.q = (const T *)c.q;
   if constexpr (DFM) {
@@ -483,6 +487,7 @@ template <typename T, bool DFM> static PArgs<T> fill_args(Poisson *p, const Ctx 
   a.status = c.status;
   a.part = p->part;
   a.bar = p->bar;
+  a.spin_limit = p->spin_limit;
   return a;
 }
 
@@ -503,9 +508,56 @@ template <typename T, bool DFM> static int persistent_launch(Poisson *p, Ctx &c,
   return cudaLaunchKernelEx(&cfg, k_poisson<T, DFM>, a) == cudaSuccess ? 0 : -1;
 }
 
+static double eps_range(const Ctx &c, double *lo) {
+  double mn = std::min(c.eps_a, c.ncomp == 2 ? c.eps_b : c.eps_a), mx = std::max(c.eps_a, c.ncomp == 2 ? c.eps_b : c.eps_a);
+  if (c.ncoll_max > 0) {
+    mn = std::min(mn, c.eps_p);
+    mx = std::max(mx, c.eps_p);
+  }
+  *lo = mn;
+  return mx;
+}
+
+bool poisson_spectral_choice(const Ctx &c, int fp64) {
+  if (c.psolver == LBEH_POISSON_MULTIGRID) return false;
+  if (!spectral_supported(c.d, fp64)) return false;
+  if (c.psolver == LBEH_POISSON_SPECTRAL) return true;
+  double lo = 0.0;
+  const double hi = eps_range(c, &lo);
+  return c.ncoll_max == 0 && lo > 0.0 && hi / lo <= kSpectralMaxContrast;
+}
+
+bool poisson_is_spectral(const Poisson *p) { return p->spec != nullptr; }
+void poisson_set_wait_limit(Poisson *p, long long polls) { p->spin_limit = polls > 0 ? polls : kSpinLimit; }
+
 Poisson *poisson_create(const Ctx &c, int fp64) {
   Poisson *p = new Poisson;
   p->fp64 = fp64;
+  if (poisson_spectral_choice(c, fp64)) {
+    double lo = 0.0;
+    const double hi = eps_range(c, &lo);
+    p->spec = spectral_create(c, fp64, 0.5 * (lo + hi));
+    if (!p->spec) {
+      delete p;
+      return nullptr;
+    }
+    if (fp64)
+      p->phi_prev = alloc<double>(p, c.d.N);
+    else {
+      p->prev_hi = alloc<float>(p, c.d.N);
+      p->prev_lo = alloc<float>(p, c.d.N);
+    }
+    p->dev = alloc<PDev>(p, 1);
+    p->bar = alloc<Bar>(p, 1);
+    p->part = alloc<double>(p, 3 * spectral_grid(p->spec) + 8);
+    if ((fp64 ? !p->phi_prev : (!p->prev_hi || !p->prev_lo)) || !p->dev || !p->bar || !p->part) {
+      poisson_destroy(p);
+      return nullptr;
+    }
+    cudaMemset(p->bar, 0, sizeof(Bar));
+    cudaMemset(p->dev, 0, sizeof(PDev));
+    return p;
+  }
   bool ok = fp64 ? setup<double>(p, c.d) : setup<float>(p, c.d);
   if (fp64) {
     p->phi_prev = alloc<double>(p, c.d.N);
@@ -535,6 +587,7 @@ Poisson *poisson_create(const Ctx &c, int fp64) {
 
 void poisson_destroy(Poisson *p) {
   if (!p) return;
+  spectral_destroy(p->spec);
   for (void *a : p->allocs) cudaFree(a);
   delete p;
 }
@@ -596,11 +649,20 @@ static int enqueue(Poisson *p, Ctx &c, cudaGraphConditionalHandle handle, bool g
   auto &L = levels<T>(p);
   const Dims d = c.d;
   const cudaStream_t s = c.s;
-  Level<T> &l0 = L[0];
   constexpr bool DFM = std::is_same<T, float>::value;  // double-float potential
-  if (p->pgrid > 0) {
+  if (p->spec || p->pgrid > 0) {
     // whole solve in one cooperative launch
-    if (persistent_launch<T, DFM>(p, c, s) != 0) return -1;
+    if (p->spec) {
+      const PArgs<T> a = fill_args<T, DFM>(p, c);
+      int rc;
+      if constexpr (DFM)
+        rc = spectral_launch_f32(p->spec, c, a, s);
+      else
+        rc = spectral_launch_f64(p->spec, c, a, s);
+      if (rc != 0) return -1;
+    } else if (persistent_launch<T, DFM>(p, c, s) != 0) {
+      return -1;
+    }
     p->body_launches = 0;
     if (graph) return 0;
     PDev hd{};
@@ -609,6 +671,7 @@ static int enqueue(Poisson *p, Ctx &c, cudaGraphConditionalHandle handle, bool g
     *relres = hd.relres;
     return hd.notconv ? -(hd.iters + 2) : hd.iters;
   }
+  Level<T> &l0 = L[0];
   float *phi_hi = (float *)c.phit, *phi_lo = c.phi_lo;
   const DF edf[3] = {df_split(c.Eext[0]), df_split(c.Eext[1]), df_split(c.Eext[2])};
   auto residual = [&](cudaStream_t st) {
@@ -745,6 +808,7 @@ template <typename T, bool DFM> static long long team_setup(Poisson *p, const Ct
 }
 
 long long poisson_team_args(Poisson *p, const Ctx &c, void *out, size_t out_bytes) {
+  if (p->spec) return -1;  // the batched step cycles the multigrid
   if (p->fp64) {
     if (out_bytes != sizeof(PArgs<double>)) return -1;
     const long long smem = team_setup<double, false>(p, c);
@@ -804,5 +868,5 @@ void phi_from_double(Ctx &c, const double *in) {
 }  // namespace lbeh
 
 namespace lbeh {
-bool poisson_needs_conditional(const Poisson *p) { return p->pgrid == 0; }
+bool poisson_needs_conditional(const Poisson *p) { return p->pgrid == 0 && !p->spec; }
 }  // namespace lbeh

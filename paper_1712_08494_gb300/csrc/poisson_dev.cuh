@@ -552,9 +552,9 @@ __device__ void tail_vcycle(const Level<T> *__restrict__ lv, int n, int first, u
 // take the same branches.  The barrier wait is bounded: a block that gives up
 // raises an abort flag and the device status, and every block then returns.
 constexpr int kPB = 512;
-constexpr long long kSpinLimit = 1LL << 24;
+constexpr long long kSpinLimit = 1LL << 24;  // default polls of a barrier wait (~100 ns each: about two seconds)
 constexpr double kTrustTol = 1e-8;  // FP32 residual estimate used only above this tolerance
-constexpr double kEstErr = 1e-4;    // bound of its error relative to the last exact residual  // polls of ~100 ns: about two seconds
+constexpr double kEstErr = 1e-4;    // bound of its error relative to the last exact residual
 
 struct Bar {
   unsigned long long arrived;  // monotonic arrival count (reset before each launch)
@@ -582,7 +582,7 @@ __device__ __forceinline__ int ld_acquire_s32(const int *p) {
 // preceding __syncthreads) and polls it with acquire loads until all blocks of
 // this barrier generation have arrived.  The wait is bounded; on time-out the block raises
 // the abort flag and the status, and every block leaves at its next barrier.
-__device__ __forceinline__ bool grid_sync(Bar *bar, int *status) {
+__device__ __forceinline__ bool grid_sync(Bar *bar, int *status, long long spin_limit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -592,7 +592,7 @@ __device__ __forceinline__ bool grid_sync(Bar *bar, int *status) {
     long long spins = 0;
     while (ld_acquire_u64(&bar->arrived) < target) {
       if (ld_acquire_s32(&bar->abort)) break;
-      if (++spins > kSpinLimit) {
+      if (++spins > spin_limit) {
         atomicExch(&bar->abort, 1);
         atomicOr(status, ST_TIMEOUT);
         break;
@@ -613,11 +613,12 @@ __device__ __forceinline__ bool grid_sync(Bar *bar, int *status) {
 struct GridTeam {
   Bar *bar;
   int *status;
+  long long spin_limit;  // polls of a barrier wait before the solve gives up
   __device__ long long rank() const { return blockIdx.x * (long long)blockDim.x + threadIdx.x; }
   __device__ long long size() const { return (long long)gridDim.x * blockDim.x; }
   __device__ int block() const { return blockIdx.x; }
   __device__ int nblocks() const { return gridDim.x; }
-  __device__ bool sync() const { return grid_sync(bar, status); }
+  __device__ bool sync() const { return grid_sync(bar, status, spin_limit); }
 };
 
 struct ClusterTeam {
@@ -649,6 +650,7 @@ template <typename T> struct PArgs {
   int *status;
   double *part;  // [3][blocks of the team]
   Bar *bar;
+  long long spin_limit;  // polls of a grid-barrier wait before time-out (cooperative solve)
 };
 
 __device__ __forceinline__ double block_sum_n(double v, double *sh) {
@@ -972,12 +974,13 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
     st->relres = rr;
     st->iters = it;
     st->total_iters += it;
-    const int fail = rr >= tol;
+    const int fail = !(rr < tol);  // not converged, or not finite
     st->notconv = fail;
     st->cond = 0;
     st->zero = zero;
     st->have_prev = 1;
     if (fail) atomicOr(a.status, ST_POISSON);
+    if (!isfinite(rr)) atomicOr(a.status, ST_NONFINITE);
   }
 }
 

@@ -1,19 +1,28 @@
-// Constant-coefficient inverse z = (eps0 L)^-1 r of the periodic seven-point
-// Laplacian L by separable discrete Hartley transforms: the inner solve of
-// the spectral split of Sec. II.D (eps0 L phi^{k+1} = b - div((eps - eps0)
-// grad phi^k)) and the preconditioner of a conjugate-gradient solve of the
-// variable-permittivity equation.  The discrete Hartley transform H[k] =
-// Re F[k] - Im F[k] of a real line is real, is its own inverse up to 1/N and,
-// applied along x, y and z, diagonalises L with the eigenvalues
+// Constant-coefficient inverse z = (eps_ref L)^-1 r of the periodic seven-point
+// Laplacian L by separable discrete Hartley transforms.  Sec. II.D solves the
+// Poisson equation with a Fourier spectral method; at variable permittivity
+// this library uses that constant-coefficient inverse as the preconditioner
+// of a conjugate-gradient solve of the flux-form equation (eps_ref is a
+// reference permittivity of the box, not the vacuum permittivity of
+// Sec. II.B).  The discrete Hartley transform H[k] = Re F[k] - Im F[k] of a
+// real line is real and is its own inverse up to 1/N; applied along x, y and z
+// it diagonalises L with the eigenvalues
 // Lambda(k) = -sum_a 2 (1 - cos(2 pi k_a / n_a)).
 //
-// Line transform: mixed-radix Stockham FFT (radices 8, 4, 2 with explicit
-// butterflies, 3, 5, 7 generic) of the real line.  Lattice passes: tiles of
-// 32 lines of the pass axis staged in shared memory with coalesced global
-// accesses; five passes H_x, H_y, [H_z, scale, H_z], H_y, H_x.
+// Line transforms: mixed-radix Stockham FFT (radices 8, 4, 2 with explicit
+// butterflies, 3, 5, 7 generic) of a complex line that packs two real lines
+// (z = a + i b); the Hartley transforms of a and b follow from Z[k] and
+// Z[N-k]:  H_a[k] = (P[k] + M[N-k]) / 2,  H_b[k] = (M[k] - P[N-k]) / 2 with
+// P = Re Z - Im Z and M = Re Z + Im Z.
 //
-// Header only; the step does not call it yet (the multigrid solves Sec. II.B).
-// The same line and tile functions run on the host in the tests.
+// Lattice passes: a tile of W lines of the pass axis is staged in shared
+// memory (W consecutive rows for x; W consecutive x at fixed (z) or (y) for
+// the y and z passes, so global accesses are coalesced along x), each warp
+// transforms its pairs of lines, and the tile is written back in place.  The
+// z pass can apply the symbol and transform again (forward, scale, inverse).
+//
+// The line and tile functions are __host__ __device__: the tests run them on
+// the host with the same index arithmetic as the device solver.
 #pragma once
 #ifndef LBEH_SPEC_HD
 #ifdef __CUDACC__
@@ -25,11 +34,16 @@
 
 namespace lbeh_spectral {
 
-struct cf {
-  float x, y;
+template <typename T> struct C2 {
+  T x, y;
 };
-LBEH_SPEC_HD cf cadd(cf a, cf b) { return cf{a.x + b.x, a.y + b.y}; }
-LBEH_SPEC_HD cf cmul(cf a, cf b) { return cf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+template <typename T> LBEH_SPEC_HD C2<T> cadd(C2<T> a, C2<T> b) { return C2<T>{a.x + b.x, a.y + b.y}; }
+template <typename T> LBEH_SPEC_HD C2<T> csub(C2<T> a, C2<T> b) { return C2<T>{a.x - b.x, a.y - b.y}; }
+template <typename T> LBEH_SPEC_HD C2<T> cmul(C2<T> a, C2<T> b) {
+  return C2<T>{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename T> LBEH_SPEC_HD C2<T> mul_mi(C2<T> a) { return C2<T>{a.y, -a.x}; }  // a * (-i)
+using cf = C2<float>;
 
 constexpr int kMaxStages = 12;
 constexpr int kMaxN = 512;
@@ -48,219 +62,157 @@ LBEH_SPEC_HD int factorize(int N, int *rad) {
   return n == 1 ? m : 0;
 }
 
-// small DFTs (forward, exp(-2 pi i / R) convention); generic for 3, 5, 7
-LBEH_SPEC_HD cf mul_mi(cf a) { return cf{a.y, -a.x}; }  // a * (-i)
-template <int R> LBEH_SPEC_HD void dft_small(cf *v, const cf *w, int stride) {
-  cf o[R];
-  for (int a = 0; a < R; ++a) {
-    cf s = v[0];
-    for (int b = 1; b < R; ++b) s = cadd(s, cmul(v[b], w[((a * b) % R) * stride]));
-    o[a] = s;
+// small DFTs (forward, exp(-2 pi i / R) convention); generic for 3, 5, 7 with
+// the R-th roots taken from the line's root table w (w[t] = exp(-2 pi i t / N))
+template <typename T, int R> struct Dft {
+  LBEH_SPEC_HD static void run(C2<T> *v, const C2<T> *w, int stride) {
+    C2<T> o[R];
+    for (int a = 0; a < R; ++a) {
+      C2<T> s = v[0];
+      for (int b = 1; b < R; ++b) s = cadd(s, cmul(v[b], w[((a * b) % R) * stride]));
+      o[a] = s;
+    }
+    for (int a = 0; a < R; ++a) v[a] = o[a];
   }
-  for (int a = 0; a < R; ++a) v[a] = o[a];
-}
-template <> LBEH_SPEC_HD void dft_small<2>(cf *v, const cf *, int) {
-  const cf a = v[0], b = v[1];
-  v[0] = cadd(a, b);
-  v[1] = cf{a.x - b.x, a.y - b.y};
-}
-template <> LBEH_SPEC_HD void dft_small<4>(cf *v, const cf *, int) {
-  const cf s02 = cadd(v[0], v[2]), d02 = cf{v[0].x - v[2].x, v[0].y - v[2].y};
-  const cf s13 = cadd(v[1], v[3]), d13 = mul_mi(cf{v[1].x - v[3].x, v[1].y - v[3].y});
-  v[0] = cadd(s02, s13);
-  v[2] = cf{s02.x - s13.x, s02.y - s13.y};
-  v[1] = cadd(d02, d13);
-  v[3] = cf{d02.x - d13.x, d02.y - d13.y};
-}
-template <> LBEH_SPEC_HD void dft_small<8>(cf *v, const cf *, int) {
-  // two radix-4 DFTs of the even and odd samples joined by the eighth roots
-  cf e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
-  dft_small<4>(e, nullptr, 0);
-  dft_small<4>(o, nullptr, 0);
-  const float h = 0.70710678118654752f;
-  const cf t1 = cf{h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};  // o1 * exp(-i pi/4)
-  const cf t2 = mul_mi(o[2]);                                       // o2 * exp(-i pi/2)
-  const cf t3 = cf{h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y)};  // o3 * exp(-3 i pi/4)
-  const cf t[4] = {o[0], t1, t2, t3};
-  for (int k = 0; k < 4; ++k) {
-    v[k] = cadd(e[k], t[k]);
-    v[k + 4] = cf{e[k].x - t[k].x, e[k].y - t[k].y};
+};
+template <typename T> struct Dft<T, 2> {
+  LBEH_SPEC_HD static void run(C2<T> *v, const C2<T> *, int) {
+    const C2<T> a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
   }
-}
+};
+template <typename T> struct Dft<T, 4> {
+  LBEH_SPEC_HD static void run(C2<T> *v, const C2<T> *, int) {
+    const C2<T> s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+    const C2<T> s13 = cadd(v[1], v[3]), d13 = mul_mi(csub(v[1], v[3]));
+    v[0] = cadd(s02, s13);
+    v[2] = csub(s02, s13);
+    v[1] = cadd(d02, d13);
+    v[3] = csub(d02, d13);
+  }
+};
+template <typename T> struct Dft<T, 8> {
+  LBEH_SPEC_HD static void run(C2<T> *v, const C2<T> *, int) {
+    // two radix-4 DFTs of the even and odd samples joined by the eighth roots
+    C2<T> e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    Dft<T, 4>::run(e, nullptr, 0);
+    Dft<T, 4>::run(o, nullptr, 0);
+    const T h = T(0.70710678118654752440);
+    const C2<T> t1{h * (o[1].x + o[1].y), h * (o[1].y - o[1].x)};  // o1 * exp(-i pi/4)
+    const C2<T> t2 = mul_mi(o[2]);                                 // o2 * exp(-i pi/2)
+    const C2<T> t3{h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y)};  // o3 * exp(-3 i pi/4)
+    const C2<T> t[4] = {o[0], t1, t2, t3};
+    for (int k = 0; k < 4; ++k) {
+      v[k] = cadd(e[k], t[k]);
+      v[k + 4] = csub(e[k], t[k]);
+    }
+  }
+};
 
 // one butterfly j (0 <= j < N/R) of the Stockham stage with radix R after
 // sub-transforms of size Ns; w[t] = exp(-2 pi i t / N)
-template <int R> LBEH_SPEC_HD void stage_bfly_r(const cf *in, cf *out, const cf *w, int N, int Ns, int j) {
-  cf v[R];
+template <typename T, int R>
+LBEH_SPEC_HD void stage_bfly_r(const C2<T> *in, C2<T> *out, const C2<T> *w, int N, int Ns, int j) {
+  C2<T> v[R];
   const int stride = N / R;
   const int jn = j % Ns;
   const int tstep = N / (Ns * R);  // twiddle index unit of this stage
   v[0] = in[j];
   for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * stride], w[(jn * r * tstep) % N]);
-  dft_small<R>(v, w, stride);
+  Dft<T, R>::run(v, w, stride);
   const int idx = (j / Ns) * Ns * R + jn;
   for (int a = 0; a < R; ++a) out[idx + a * Ns] = v[a];
 }
-LBEH_SPEC_HD void stage_bfly(const cf *in, cf *out, const cf *w, int N, int R, int Ns, int j) {
+template <typename T>
+LBEH_SPEC_HD void stage_bfly(const C2<T> *in, C2<T> *out, const C2<T> *w, int N, int R, int Ns, int j) {
   switch (R) {
-    case 2: stage_bfly_r<2>(in, out, w, N, Ns, j); break;
-    case 3: stage_bfly_r<3>(in, out, w, N, Ns, j); break;
-    case 4: stage_bfly_r<4>(in, out, w, N, Ns, j); break;
-    case 5: stage_bfly_r<5>(in, out, w, N, Ns, j); break;
-    case 7: stage_bfly_r<7>(in, out, w, N, Ns, j); break;
-    default: stage_bfly_r<8>(in, out, w, N, Ns, j); break;
+    case 2: stage_bfly_r<T, 2>(in, out, w, N, Ns, j); break;
+    case 3: stage_bfly_r<T, 3>(in, out, w, N, Ns, j); break;
+    case 4: stage_bfly_r<T, 4>(in, out, w, N, Ns, j); break;
+    case 5: stage_bfly_r<T, 5>(in, out, w, N, Ns, j); break;
+    case 7: stage_bfly_r<T, 7>(in, out, w, N, Ns, j); break;
+    default: stage_bfly_r<T, 8>(in, out, w, N, Ns, j); break;
   }
 }
 
-// whole transform on the host (reference driver of the same stages)
-inline void dht_host(const float *x, float *h, int N, const cf *w, cf *b0, cf *b1) {
+// Hartley values at positions k and N-k of the two real lines packed in the
+// transformed complex line Z: (H_a[k], H_b[k], H_a[N-k], H_b[N-k])
+template <typename T> struct Split {
+  T ak, bk, an, bn;
+};
+template <typename T> LBEH_SPEC_HD Split<T> pair_split(const C2<T> *Z, int N, int k) {
+  const int kn = k == 0 ? 0 : N - k;
+  const C2<T> zk = Z[k], zn = Z[kn];
+  const T Pk = zk.x - zk.y, Mk = zk.x + zk.y, Pn = zn.x - zn.y, Mn = zn.x + zn.y;
+  return Split<T>{T(0.5) * (Pk + Mn), T(0.5) * (Mk - Pn), T(0.5) * (Pn + Mk), T(0.5) * (Mn - Pk)};
+}
+
+// whole transform of one complex line on the host (reference driver of the
+// same stages); returns the buffer holding the result
+template <typename T> inline C2<T> *fft_host(C2<T> *b0, C2<T> *b1, int N, const C2<T> *w) {
   int rad[kMaxStages];
   const int m = factorize(N, rad);
-  for (int i = 0; i < N; ++i) b0[i] = cf{x[i], 0.f};
-  cf *in = b0, *out = b1;
+  C2<T> *in = b0, *out = b1;
   int Ns = 1;
   for (int s = 0; s < m; ++s) {
     for (int j = 0; j < N / rad[s]; ++j) stage_bfly(in, out, w, N, rad[s], Ns, j);
     Ns *= rad[s];
-    cf *t = in;
+    C2<T> *t = in;
     in = out;
     out = t;
   }
-  for (int k = 0; k < N; ++k) h[k] = in[k].x - in[k].y;
+  return in;
 }
 
-}  // namespace lbeh_spectral
+// Hartley transform of one real line on the host (imaginary part zero)
+inline void dht_host(const float *x, float *h, int N, const cf *w, cf *b0, cf *b1) {
+  for (int i = 0; i < N; ++i) b0[i] = cf{x[i], 0.f};
+  const cf *Z = fft_host(b0, b1, N, w);
+  for (int k = 0; k < N; ++k) h[k] = Z[k].x - Z[k].y;
+}
 
-namespace lbeh_spectral {
-
-constexpr int kTileLines = 32;
-constexpr int kWarps = 8;
-
-struct AxisPlan {
-  int n;                // line length
-  int nrad;             // stages
-  int rad[kMaxStages];  // radices
-  const cf *w;          // n roots exp(-2 pi i t / n) in global memory
-};
-
+// ---------------------------------------------------------------- tiles
 struct Grid3 {
   int nx, ny, nz;
 };
 
-// element (line l, position p) of tile t along axis A
-template <int A> LBEH_SPEC_HD long long tile_index(const Grid3 &g, int t, int l, int p, bool &ok) {
-  if (A == 0) {  // lines are rows: line = t*32 + l over (y, z), position = x
-    const int line = t * kTileLines + l;
-    ok = line < g.ny * g.nz;
-    return (long long)line * g.nx + p;
+// Tiles of W lines along axis A.  A = 0: lines are the rows (y, z), tile t
+// holds rows t*W .. t*W+W-1.  A = 1 / 2: lines are the columns at fixed z (A =
+// 1) or fixed y (A = 2), tile t holds x = xb*W .. xb*W+W-1 with xb = t % xt.
+LBEH_SPEC_HD int line_len(const Grid3 &g, int A) { return A == 0 ? g.nx : (A == 1 ? g.ny : g.nz); }
+LBEH_SPEC_HD int tile_count(const Grid3 &g, int A, int W) {
+  if (A == 0) return (g.ny * g.nz + W - 1) / W;
+  const int xt = (g.nx + W - 1) / W;
+  return xt * (A == 1 ? g.nz : g.ny);
+}
+// global index of element (line l, position p) of tile t; ok = line exists
+LBEH_SPEC_HD long long tile_index(const Grid3 &g, int A, int W, int t, int l, int p, bool &ok) {
+  if (A == 0) {
+    const long long line = (long long)t * W + l;
+    ok = line < (long long)g.ny * g.nz;
+    return line * g.nx + p;
   }
-  // lines are columns x0 + l at fixed (z) for A = 1 (position y) or fixed (y) for A = 2 (position z)
-  const int xt = (g.nx + kTileLines - 1) / kTileLines;
-  const int x = (t % xt) * kTileLines + l;
+  const int xt = (g.nx + W - 1) / W;
+  const int x = (t % xt) * W + l;
   const int o = t / xt;  // z for A = 1, y for A = 2
   ok = x < g.nx;
   if (A == 1) return ((long long)o * g.ny + p) * g.nx + x;
   return ((long long)p * g.ny + o) * g.nx + x;
 }
-
-template <int A> LBEH_SPEC_HD int tile_count(const Grid3 &g) {
-  if (A == 0) return (g.ny * g.nz + kTileLines - 1) / kTileLines;
-  const int xt = (g.nx + kTileLines - 1) / kTileLines;
-  return xt * (A == 1 ? g.nz : g.ny);
+// wavenumbers (kx, ky) of line l of a z-pass tile (after the x and y passes)
+LBEH_SPEC_HD void zline_k(const Grid3 &g, int W, int t, int l, int &kx, int &ky) {
+  const int xt = (g.nx + W - 1) / W;
+  kx = (t % xt) * W + l;
+  ky = t / xt;
 }
 
-// Lambda(k) = -sum_a 2 (1 - cos(2 pi k_a / n_a)) of the seven-point Laplacian
-LBEH_SPEC_HD float lap_symbol(const Grid3 &g, int kx, int ky, int kz, const float *cx, const float *cy, const float *cz) {
-  return -(cx[kx] + cy[ky] + cz[kz]);
-}
-
-}  // namespace lbeh_spectral
-
-#ifdef __CUDACC__
-namespace lbeh_spectral {
-
-// one warp transforms line l of the staged tile in place (real -> real)
-__device__ __forceinline__ void warp_line_dht(float *tile_line, int stride, const AxisPlan &P, cf *b0, cf *b1,
-                                              int lane) {
-  const int N = P.n;
-  for (int i = lane; i < N; i += 32) b0[i] = cf{tile_line[i * stride], 0.f};
-  __syncwarp();
-  cf *in = b0, *out = b1;
-  int Ns = 1;
-  for (int s = 0; s < P.nrad; ++s) {
-    const int R = P.rad[s];
-    for (int j = lane; j < N / R; j += 32) stage_bfly(in, out, P.w, N, R, Ns, j);
-    __syncwarp();
-    Ns *= R;
-    cf *t = in;
-    in = out;
-    out = t;
-  }
-  for (int i = lane; i < N; i += 32) tile_line[i * stride] = in[i].x - in[i].y;
-  __syncwarp();
-}
-
-// pass along axis A; for the z pass (A == 2) with fuse set, the forward
-// transform, the scale and the inverse transform run on the staged tile
-template <int A>
-__global__ void __launch_bounds__(kWarps * 32) k_dht_pass(float *u, Grid3 g, AxisPlan P, bool fuse, float inv_eps0_n,
-                                                          const float *cx, const float *cy, const float *cz) {
-  extern __shared__ float smem[];
-  const int N = P.n;
-  float *tile = smem;                                    // [kTileLines][N] (line-major)
-  cf *bufs = reinterpret_cast<cf *>(smem + kTileLines * N);  // per warp 2 N complex
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  cf *b0 = bufs + warp * 2 * N, *b1 = b0 + N;
-  const int ntiles = tile_count<A>(g);
-  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    // stage: consecutive threads read consecutive addresses
-    for (int e = threadIdx.x; e < kTileLines * N; e += blockDim.x) {
-      int l, p;
-      if (A == 0) {
-        l = e / N;
-        p = e % N;
-      } else {
-        l = e % kTileLines;
-        p = e / kTileLines;
-      }
-      bool ok;
-      const long long gi = tile_index<A>(g, t, l, p, ok);
-      tile[l * N + p] = ok ? u[gi] : 0.f;
-    }
-    __syncthreads();
-    for (int l = warp; l < kTileLines; l += kWarps) {
-      warp_line_dht(tile + l * N, 1, P, b0, b1, lane);
-      if (A == 2 && fuse) {
-        // position p is kz; (x, y) of the tile line are (kx, ky) after the x and y passes
-        const int xt = (g.nx + kTileLines - 1) / kTileLines;
-        const int kx = (t % xt) * kTileLines + l, ky = t / xt;
-        if (kx < g.nx) {
-          for (int p = lane; p < N; p += 32) {
-            const float lam = lap_symbol(g, kx, ky, p, cx, cy, cz);
-            tile[l * N + p] = (kx == 0 && ky == 0 && p == 0) ? 0.f : tile[l * N + p] * inv_eps0_n / lam;
-          }
-        }
-        __syncwarp();
-        warp_line_dht(tile + l * N, 1, P, b0, b1, lane);
-      }
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < kTileLines * N; e += blockDim.x) {
-      int l, p;
-      if (A == 0) {
-        l = e / N;
-        p = e % N;
-      } else {
-        l = e % kTileLines;
-        p = e / kTileLines;
-      }
-      bool ok;
-      const long long gi = tile_index<A>(g, t, l, p, ok);
-      if (ok) u[gi] = tile[l * N + p];
-    }
-    __syncthreads();
-  }
+// scale of the symbol step: 1 / (eps_ref Lambda(k) N_sites), zero mode 0;
+// s_a[k] = 2 (1 - cos(2 pi k / n_a))
+template <typename T>
+LBEH_SPEC_HD T inv_symbol(int kx, int ky, int kz, const T *sx, const T *sy, const T *sz, T inv_eref_n) {
+  if (kx == 0 && ky == 0 && kz == 0) return T(0);
+  return -inv_eref_n / (sx[kx] + sy[ky] + sz[kz]);
 }
 
 }  // namespace lbeh_spectral
-#endif

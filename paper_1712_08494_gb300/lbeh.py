@@ -28,6 +28,8 @@ LBEH_ERR_UNSUPPORTED = -7
 LBEH_FP64, LBEH_FP32, LBEH_FP32_BF16STORE, LBEH_FP32_FP16STORE = 0, 1, 2, 3
 PREC = {"fp64": LBEH_FP64, "fp32": LBEH_FP32, "bf16": LBEH_FP32_BF16STORE, "fp16": LBEH_FP32_FP16STORE}
 LBEH_F64, LBEH_F32 = 0, 1
+LBEH_POISSON_AUTO, LBEH_POISSON_MULTIGRID, LBEH_POISSON_SPECTRAL = 0, 1, 2
+SOLVER = {"auto": LBEH_POISSON_AUTO, "multigrid": LBEH_POISSON_MULTIGRID, "spectral": LBEH_POISSON_SPECTRAL}
 
 LBEH_AUX_SOLID, LBEH_AUX_OWNER, LBEH_AUX_PSI_S, LBEH_AUX_SURFACE = 0, 1, 2, 3
 LBEH_AUX_QC, LBEH_AUX_EPS, LBEH_AUX_Q, LBEH_AUX_RHO_V, LBEH_AUX_U = 4, 5, 6, 7, 8
@@ -35,7 +37,7 @@ LBEH_AUX_QC, LBEH_AUX_EPS, LBEH_AUX_Q, LBEH_AUX_RHO_V, LBEH_AUX_U = 4, 5, 6, 7, 
 # exported symbols declared in include/lbeh.h
 SYMBOLS = ("lbeh_create", "lbeh_set_fields", "lbeh_get_fields", "lbeh_step", "lbeh_observables",
            "lbeh_get_aux", "lbeh_profile_enable", "lbeh_profile_read", "lbeh_observables_noalloc",
-           "lbeh_last_error", "lbeh_destroy", "lbeh_status_string")
+           "lbeh_last_error", "lbeh_destroy", "lbeh_status_string", "lbeh_set_wait_limit")
 LBEH_NOALLOC_MAX_SITES = 16777216
 
 LBEH_STAGE_MACRO, LBEH_STAGE_POISSON, LBEH_STAGE_COLLIDE, LBEH_STAGE_NP, LBEH_STAGE_COLLOID = 0, 1, 2, 3, 4
@@ -53,6 +55,7 @@ class lbeh_params(C.Structure):
         ("E_ext", C.c_double * 3), ("poisson_tol", C.c_double), ("poisson_max_iter", C.c_int),
         ("ncolloid_max", C.c_int), ("rho_p", C.c_double), ("k_hertz", C.c_double),
         ("psi_subdiv", C.c_int), ("colloids_move", C.c_int), ("stream", C.c_void_p),
+        ("poisson_solver", C.c_int),
     ]
 
 
@@ -73,7 +76,7 @@ class lbeh_obs(C.Structure):
         ("mass", C.c_double * 2), ("ions", C.c_double * 2), ("charge", C.c_double),
         ("momentum", C.c_double * 3), ("deformation", C.c_double), ("centroid", C.c_double * 3),
         ("colloid_v", C.c_double * 3), ("poisson_relres", C.c_double), ("poisson_iters", C.c_int),
-        ("status", C.c_int), ("steps", C.c_longlong),
+        ("status", C.c_int), ("steps", C.c_longlong), ("poisson_solver", C.c_int),
     ]
 
 
@@ -115,6 +118,7 @@ def _load():
     lib.lbeh_batch_set_shape.argtypes = [H, C.c_int]
     lib.lbeh_batch_shape.argtypes = [H]
     lib.lbeh_step_adjoint.argtypes = [H, C.c_int, C.c_int, C.POINTER(lbeh_obs_seed), C.POINTER(lbeh_grads)]
+    lib.lbeh_set_wait_limit.argtypes = [H, C.c_longlong]
     lib.lbeh_destroy.argtypes = [H]
     lib.lbeh_destroy.restype = None
     lib.lbeh_last_error.argtypes = [H]
@@ -251,6 +255,10 @@ def lbeh_batch_shape(h) -> int:
     return int(_lib.lbeh_batch_shape(h))
 
 
+def lbeh_set_wait_limit(h, polls: int) -> int:
+    return _check(_lib.lbeh_set_wait_limit(h, int(polls)), "lbeh_set_wait_limit")
+
+
 def lbeh_destroy(h) -> None:
     _lib.lbeh_destroy(h)
 
@@ -276,6 +284,8 @@ def make_params(p, stream: int = 0) -> lbeh_params:
     c.rho_p, c.k_hertz = float(p.rho_p), float(p.k_hertz)
     c.psi_subdiv, c.colloids_move = int(p.psi_subdiv), int(p.colloids_move)
     c.stream = int(stream) or None
+    sv = getattr(p, "poisson_solver", "auto")
+    c.poisson_solver = SOLVER[sv] if isinstance(sv, str) else int(sv)
     return c
 
 

@@ -48,6 +48,7 @@ class Params:
     k_hertz: float = 1.0
     psi_subdiv: int = 3
     colloids_move: int = 0
+    poisson_solver: str = "auto"  # auto | multigrid | spectral
 
     def as_dict(self) -> dict:
         return asdict(self)

@@ -1,82 +1,118 @@
 // Host driver of the spectral transform core (csrc/spectral.cuh) for the
-// tests: the line transform, and the five lattice passes with the same tile
-// staging and index helpers as the device kernels, run block by block.
+// tests: the line transform, and the five lattice passes of the
+// preconditioner with the same tile indexing, pairing of real lines into
+// complex lines, Hartley split and symbol scaling as the device solver, run
+// tile by tile.
 #include <cmath>
 #include <vector>
 
 #include "spectral.cuh"
 using namespace lbeh_spectral;
 
-template <int A>
-static void pass_host(float *u, const Grid3 &g, int N, const std::vector<cf> &w, bool fuse, float inv_eps0_n,
-                      const float *cx, const float *cy, const float *cz) {
-  std::vector<float> tile(kTileLines * N), line(N), out(N);
-  std::vector<cf> b0(N), b1(N);
-  const int nt = tile_count<A>(g);
-  for (int t = 0; t < nt; ++t) {
-    for (int l = 0; l < kTileLines; ++l)
-      for (int p = 0; p < N; ++p) {
-        bool ok;
-        const long long gi = tile_index<A>(g, t, l, p, ok);
-        tile[l * N + p] = ok ? u[gi] : 0.f;
-      }
-    for (int l = 0; l < kTileLines; ++l) {
-      dht_host(&tile[l * N], out.data(), N, w.data(), b0.data(), b1.data());
-      for (int p = 0; p < N; ++p) tile[l * N + p] = out[p];
-      if (A == 2 && fuse) {
-        const int xt = (g.nx + kTileLines - 1) / kTileLines;
-        const int kx = (t % xt) * kTileLines + l, ky = t / xt;
-        if (kx < g.nx)
-          for (int p = 0; p < N; ++p) {
-            const float lam = lap_symbol(g, kx, ky, p, cx, cy, cz);
-            tile[l * N + p] = (kx == 0 && ky == 0 && p == 0) ? 0.f : tile[l * N + p] * inv_eps0_n / lam;
-          }
-        dht_host(&tile[l * N], out.data(), N, w.data(), b0.data(), b1.data());
-        for (int p = 0; p < N; ++p) tile[l * N + p] = out[p];
-      }
-    }
-    for (int l = 0; l < kTileLines; ++l)
-      for (int p = 0; p < N; ++p) {
-        bool ok;
-        const long long gi = tile_index<A>(g, t, l, p, ok);
-        if (ok) u[gi] = tile[l * N + p];
-      }
-  }
-}
-
-static std::vector<cf> roots(int n) {
-  std::vector<cf> w(n);
+template <typename T> static std::vector<C2<T>> roots(int n) {
+  std::vector<C2<T>> w(n);
   for (int t = 0; t < n; ++t) {
     const double a = -2.0 * M_PI * t / n;
-    w[t] = cf{float(std::cos(a)), float(std::sin(a))};
+    w[t] = C2<T>{T(std::cos(a)), T(std::sin(a))};
   }
   return w;
 }
-static std::vector<float> symb(int n) {
-  std::vector<float> c(n);
-  for (int k = 0; k < n; ++k) c[k] = float(2.0 * (1.0 - std::cos(2.0 * M_PI * k / n)));
+template <typename T> static std::vector<T> symb(int n) {
+  std::vector<T> c(n);
+  for (int k = 0; k < n; ++k) c[k] = T(2.0 * (1.0 - std::cos(2.0 * M_PI * k / n)));
   return c;
 }
 
-extern "C" int precond_host(float *u, int nx, int ny, int nz, double eps0) {
+template <typename T>
+static void pass_host(T *u, const Grid3 &g, int A, int W, const std::vector<C2<T>> &w, bool fuse, T inv_n,
+                      const T *sx, const T *sy, const T *sz) {
+  const int N = line_len(g, A);
+  const int pairs = W / 2;
+  std::vector<C2<T>> b0(N), b1(N), Z((size_t)pairs * N);
+  const int nt = tile_count(g, A, W);
+  for (int t = 0; t < nt; ++t) {
+    for (int m = 0; m < pairs; ++m) {
+      for (int p = 0; p < N; ++p) {
+        bool oa, ob;
+        const long long ia = tile_index(g, A, W, t, 2 * m, p, oa);
+        const long long ib = tile_index(g, A, W, t, 2 * m + 1, p, ob);
+        b0[p] = C2<T>{oa ? u[ia] : T(0), ob ? u[ib] : T(0)};
+      }
+      C2<T> *r = fft_host(b0.data(), b1.data(), N, w.data());
+      if (fuse) {
+        int kxa, kxb, ky;
+        zline_k(g, W, t, 2 * m, kxa, ky);
+        zline_k(g, W, t, 2 * m + 1, kxb, ky);
+        std::vector<C2<T>> zz(N);
+        for (int k = 0; k <= N / 2; ++k) {
+          const Split<T> s = pair_split(r, N, k);
+          const int kn = k == 0 ? 0 : N - k;
+          const T sa = kxa < g.nx ? inv_symbol(kxa, ky, k, sx, sy, sz, inv_n) : T(0);
+          const T sb = kxb < g.nx ? inv_symbol(kxb, ky, k, sx, sy, sz, inv_n) : T(0);
+          const T sa2 = kxa < g.nx ? inv_symbol(kxa, ky, kn, sx, sy, sz, inv_n) : T(0);
+          const T sb2 = kxb < g.nx ? inv_symbol(kxb, ky, kn, sx, sy, sz, inv_n) : T(0);
+          zz[k] = C2<T>{s.ak * sa, s.bk * sb};
+          zz[kn] = C2<T>{s.an * sa2, s.bn * sb2};
+        }
+        C2<T> *o = r == b0.data() ? b1.data() : b0.data();
+        for (int k = 0; k < N; ++k) o[k] = zz[k];
+        r = fft_host(o, r, N, w.data());
+      }
+      for (int p = 0; p < N; ++p) Z[(size_t)m * N + p] = r[p];
+    }
+    for (int m = 0; m < pairs; ++m)
+      for (int p = 0; p < N; ++p) {
+        const Split<T> s = pair_split(&Z[(size_t)m * N], N, p);
+        bool oa, ob;
+        const long long ia = tile_index(g, A, W, t, 2 * m, p, oa);
+        const long long ib = tile_index(g, A, W, t, 2 * m + 1, p, ob);
+        if (oa) u[ia] = s.ak;
+        if (ob) u[ib] = s.bk;
+      }
+  }
+}
+
+template <typename T> static int precond(T *u, int nx, int ny, int nz, double eps_ref, int W) {
   int r[kMaxStages];
   if (!factorize(nx, r) || !factorize(ny, r) || !factorize(nz, r)) return -1;
   Grid3 g{nx, ny, nz};
-  auto wx = roots(nx), wy = roots(ny), wz = roots(nz);
-  auto cx = symb(nx), cy = symb(ny), cz = symb(nz);
-  const float inv = float(1.0 / (eps0 * double(nx) * ny * nz));
-  pass_host<0>(u, g, nx, wx, false, 0.f, nullptr, nullptr, nullptr);
-  pass_host<1>(u, g, ny, wy, false, 0.f, nullptr, nullptr, nullptr);
-  pass_host<2>(u, g, nz, wz, true, inv, cx.data(), cy.data(), cz.data());
-  pass_host<1>(u, g, ny, wy, false, 0.f, nullptr, nullptr, nullptr);
-  pass_host<0>(u, g, nx, wx, false, 0.f, nullptr, nullptr, nullptr);
+  auto wx = roots<T>(nx), wy = roots<T>(ny), wz = roots<T>(nz);
+  auto cx = symb<T>(nx), cy = symb<T>(ny), cz = symb<T>(nz);
+  const T inv = T(1.0 / (eps_ref * double(nx) * ny * nz));
+  pass_host<T>(u, g, 0, W, wx, false, T(0), nullptr, nullptr, nullptr);
+  pass_host<T>(u, g, 1, W, wy, false, T(0), nullptr, nullptr, nullptr);
+  pass_host<T>(u, g, 2, W, wz, true, inv, cx.data(), cy.data(), cz.data());
+  pass_host<T>(u, g, 1, W, wy, false, T(0), nullptr, nullptr, nullptr);
+  pass_host<T>(u, g, 0, W, wx, false, T(0), nullptr, nullptr, nullptr);
   return 0;
+}
+
+extern "C" int precond_host(float *u, int nx, int ny, int nz, double eps_ref, int W) {
+  return precond<float>(u, nx, ny, nz, eps_ref, W);
+}
+extern "C" int precond_host_f64(double *u, int nx, int ny, int nz, double eps_ref, int W) {
+  return precond<double>(u, nx, ny, nz, eps_ref, W);
 }
 
 extern "C" int dht_line(const float *x, float *h, int N) {
   int rad[kMaxStages];
   if (!factorize(N, rad)) return -1;
-  std::vector<cf> w = roots(N), b0(N), b1(N);
+  std::vector<cf> w = roots<float>(N), b0(N), b1(N);
   dht_host(x, h, N, w.data(), b0.data(), b1.data());
+  return 0;
+}
+
+// Hartley transforms of two real lines from one complex transform
+extern "C" int dht_pair(const double *a, const double *b, double *ha, double *hb, int N) {
+  int rad[kMaxStages];
+  if (!factorize(N, rad)) return -1;
+  std::vector<C2<double>> w = roots<double>(N), b0(N), b1(N);
+  for (int i = 0; i < N; ++i) b0[i] = C2<double>{a[i], b[i]};
+  const C2<double> *Z = fft_host(b0.data(), b1.data(), N, w.data());
+  for (int k = 0; k < N; ++k) {
+    const Split<double> s = pair_split(Z, N, k);
+    ha[k] = s.ak;
+    hb[k] = s.bk;
+  }
   return 0;
 }

@@ -43,8 +43,8 @@ def test_struct_layouts_match_header(lib):
 #include "lbeh.h"
 int main(void) {
   printf("%zu %zu %zu %zu\n", sizeof(lbeh_params), sizeof(lbeh_fields), sizeof(lbeh_obs), sizeof(lbeh_profile));
-  printf("%zu %zu %zu %zu\n", offsetof(lbeh_params, E_ext), offsetof(lbeh_params, stream),
-         offsetof(lbeh_fields, ncolloid), offsetof(lbeh_obs, steps));
+  printf("%zu %zu %zu %zu %zu\n", offsetof(lbeh_params, E_ext), offsetof(lbeh_params, stream),
+         offsetof(lbeh_fields, ncolloid), offsetof(lbeh_obs, steps), offsetof(lbeh_params, poisson_solver));
   return 0;
 }
 '''
@@ -59,12 +59,14 @@ int main(void) {
     assert sizes == [C.sizeof(lib.lbeh_params), C.sizeof(lib.lbeh_fields), C.sizeof(lib.lbeh_obs),
                      C.sizeof(lib.lbeh_profile)]
     assert offs == [lib.lbeh_params.E_ext.offset, lib.lbeh_params.stream.offset,
-                    lib.lbeh_fields.ncolloid.offset, lib.lbeh_obs.steps.offset]
+                    lib.lbeh_fields.ncolloid.offset, lib.lbeh_obs.steps.offset,
+                    lib.lbeh_params.poisson_solver.offset]
 
 
 def test_invalid_parameters_are_rejected_without_a_device(lib):
     import synth
-    bad = [dict(nx=1), dict(ncomp=3), dict(nions=1), dict(prec="fp64", tau=0.5), dict(D=0.0)]
+    bad = [dict(nx=1), dict(ncomp=3), dict(nions=1), dict(prec="fp64", tau=0.5), dict(D=0.0),
+           dict(poisson_solver=3)]
     for kw in bad:
         p = synth.Params(nx=8, ny=8, nz=8)
         for k, v in kw.items():

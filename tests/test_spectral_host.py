@@ -1,9 +1,11 @@
 """Host checks of the spectral transform core (csrc/spectral.cuh): the
-mixed-radix line transform against numpy's FFT, the five tile passes as an
-exact inverse of eps0 times the periodic seven-point Laplacian on ragged
-boxes, and a conjugate-gradient solve of the oracle's variable-permittivity
-Poisson problem (Sec. II.B, II.D) preconditioned by it.  The device kernels
-of the same header are compiled for sm_103a where nvcc is present."""
+mixed-radix line transform against numpy's FFT, two real lines transformed
+as one complex line, the five tile passes (same tile indexing, line pairing
+and symbol scaling as the device solver) as an exact inverse of eps_ref times
+the periodic seven-point Laplacian on ragged boxes and odd extents, in FP32
+and FP64, and a conjugate-gradient solve of the oracle's variable-permittivity
+Poisson problem (Sec. II.B, II.D) preconditioned by it.  The device solver
+(csrc/spectral.cu) is compiled for sm_103a where nvcc is present."""
 import ctypes as C
 import os
 import shutil
@@ -26,7 +28,9 @@ def spec(tmp_path_factory):
                    check=True, capture_output=True)
     lib = C.CDLL(out)
     lib.dht_line.argtypes = [C.c_void_p, C.c_void_p, C.c_int]
-    lib.precond_host.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double]
+    lib.precond_host.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int]
+    lib.precond_host_f64.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int]
+    lib.dht_pair.argtypes = [C.c_void_p] * 4 + [C.c_int]
     return lib
 
 
@@ -50,15 +54,33 @@ def _lap(z):
     return out
 
 
-def test_lattice_passes_invert_the_laplacian(spec):
+def test_two_real_lines_from_one_complex_transform(spec):
+    rng = np.random.default_rng(2)
+    for n in (2, 3, 6, 8, 20, 35, 64, 128, 210):
+        a = rng.normal(size=n)
+        b = rng.normal(size=n)
+        ha, hb = np.zeros(n), np.zeros(n)
+        assert spec.dht_pair(a.ctypes.data, b.ctypes.data, ha.ctypes.data, hb.ctypes.data, n) == 0
+        for x, h in ((a, ha), (b, hb)):
+            f = np.fft.fft(x)
+            assert np.abs(h - (f.real - f.imag)).max() < 1e-12 * np.abs(f).max(), n
+
+
+@pytest.mark.parametrize("W", [32, 16, 8])
+def test_lattice_passes_invert_the_laplacian(spec, W):
     rng = np.random.default_rng(1)
-    for (nz, ny, nx) in ((16, 16, 16), (8, 12, 40), (24, 40, 56), (2, 6, 64), (32, 32, 48)):
+    for (nz, ny, nx) in ((16, 16, 16), (8, 12, 40), (24, 40, 56), (2, 6, 64), (32, 32, 48), (6, 10, 15), (7, 5, 9)):
         r = rng.normal(size=(nz, ny, nx)).astype(np.float32)
         z = r.copy()
-        assert spec.precond_host(z.ctypes.data, nx, ny, nz, 0.3) == 0
+        assert spec.precond_host(z.ctypes.data, nx, ny, nz, 0.3, W) == 0
         res = 0.3 * _lap(z.astype(np.float64)) - (r - r.mean())
         assert np.abs(res).max() < 2e-5 * np.abs(r).max(), (nz, ny, nx)  # FP32 transforms; an index slip gives O(1)
         assert abs(float(z.mean())) < 1e-6
+        r64 = r.astype(np.float64)
+        z64 = r64.copy()
+        assert spec.precond_host_f64(z64.ctypes.data, nx, ny, nz, 0.3, W) == 0
+        res = 0.3 * _lap(z64) - (r64 - r64.mean())
+        assert np.abs(res).max() < 1e-12 * np.abs(r64).max(), (nz, ny, nx)
 
 
 def test_preconditioned_cg_on_the_droplet_poisson_problem(spec):
@@ -76,7 +98,7 @@ def test_preconditioned_cg_on_the_droplet_poisson_problem(spec):
 
     def minv(r):
         z = r.astype(np.float32).copy()
-        spec.precond_host(z.ctypes.data, 32, 32, 32, eps0)
+        spec.precond_host(z.ctypes.data, 32, 32, 32, eps0, 32)
         return z.astype(np.float64)
 
     x = np.zeros_like(b)
@@ -105,18 +127,10 @@ def test_preconditioned_cg_on_the_droplet_poisson_problem(spec):
     assert float(np.sqrt((true * true).sum())) / bn < 2e-6
 
 
-def test_device_passes_compile_for_sm103a(tmp_path):
+def test_device_solver_compiles_for_sm103a(tmp_path):
     nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc" if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
     if nvcc is None:
         pytest.skip("nvcc not found")
-    tu = tmp_path / "spec_tu.cu"
-    tu.write_text('#include "spectral.cuh"\n'
-                  "namespace lbeh_spectral {\n"
-                  "template __global__ void k_dht_pass<0>(float *, Grid3, AxisPlan, bool, float, const float *,"
-                  " const float *, const float *);\n"
-                  "template __global__ void k_dht_pass<1>(float *, Grid3, AxisPlan, bool, float, const float *,"
-                  " const float *, const float *);\n"
-                  "template __global__ void k_dht_pass<2>(float *, Grid3, AxisPlan, bool, float, const float *,"
-                  " const float *, const float *);\n}\n")
-    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "-I", CSRC, "-c", str(tu),
-                    "-o", str(tmp_path / "spec_tu.o")], check=True, capture_output=True)
+    subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "--expt-relaxed-constexpr",
+                    "-I", CSRC, "-c", os.path.join(CSRC, "spectral.cu"), "-o", str(tmp_path / "spectral.o")],
+                   check=True, capture_output=True)
