@@ -206,56 +206,78 @@ def ncu_poisson_traffic(cycles_per_solve):
     return float(b.group(1)) / float(c.group(1)) * cycles_per_solve
 
 
-def cpu_baseline(n, budget_s=30.0):
-    """Time the FP64 CPU oracle, as it stands, on a bounded sample of the same
-    workload: one step of the droplet after one untimed step."""
+def _oracle_worker(args):
+    """One host process: the oracle stepping its own seeded copy of the droplet
+    workload; returns the wall-clock interval of the timed steps."""
+    n, seed, untimed, timed = args
+    sys.path.insert(0, ROOT)
     import synth
     from oracle import OracleSystem
-    w = synth.droplet(n=n, r=24.0 * n / 128.0, prec="fp32")
+    w = synth.droplet(n=n, r=24.0 * n / 128.0, prec="fp32", seed=seed)
     s = OracleSystem(w.params, w.rho, w.n)
-    s.step()
-    t0 = time.perf_counter()
-    s.step()
-    dt = time.perf_counter() - t0
-    return {"value": n ** 3 / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": "1 timed step (after 1 untimed) of the %d^3 droplet, numpy FP64, single thread" % n}
+    for _ in range(untimed):
+        s.step()
+    t0 = time.time()
+    for _ in range(timed):
+        s.step()
+    return t0, time.time()
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def oracle_throughput(n, untimed, timed, procs=None):
+    """The FP64 oracle, as it stands (numpy, one thread per process), on every
+    host core: one process per core, each stepping its own copy of the n^3
+    droplet.  Processes are spawned (never forked from a process that has used
+    the GPU).  Aggregate MLUPS = all sites stepped / the wall-clock span of the
+    timed steps."""
+    import multiprocessing as mp
+    procs = procs or host_cores()
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs) as pool:
+        spans = pool.map(_oracle_worker, [(n, 1 + k, untimed, timed) for k in range(procs)])
+    t0 = min(a for a, _ in spans)
+    t1 = max(b for _, b in spans)
+    return procs * n ** 3 * timed / (t1 - t0) / 1e6, procs, t1 - t0
+
+
+def cpu_baseline(n):
+    """Time the FP64 CPU oracle, as it stands, on a bounded sample of the same
+    workload: on every host core, one copy of the n^3 droplet per core, one
+    untimed step then one timed step."""
+    val, procs, span = oracle_throughput(n, 1, 1)
+    return {"value": val, "unit": "MLUPS", "cores": procs, "kind": "oracle",
+            "sample": "%d processes (one per host core), each one timed step (after one untimed) of its own %d^3 "
+                      "droplet, numpy FP64; %.1f s wall" % (procs, n, span)}
 
 
 def run_reference(args):
-    """CPU oracle timed on the host cores, each step a bounded sample (one
-    oracle step of a reduced droplet box)."""
+    """CPU oracle timed on all host cores, each step a bounded sample: every
+    core steps its own copy of a reduced droplet box."""
     rank, world, _ = env_rank()
     if rank != 0:
         return
-    import synth
-    from oracle import OracleSystem
-    n = 32
-    w = synth.droplet(n=n, r=24.0 * n / 128.0, prec="fp32")
-    s = OracleSystem(w.params, w.rho, w.n)
-    t = time.perf_counter()
-    s.step()
-    one = time.perf_counter() - t
-    while n > 8 and one * (args.steps + args.warmup) > 150.0:
+    procs = host_cores()
+    n = 64
+    # size the box so that warm-up + timed steps end within a few minutes
+    while n > 16:
+        val, _, span = oracle_throughput(n, 0, 1, procs)
+        if span * (args.steps + args.warmup) < 150.0:
+            break
         n //= 2
-        w = synth.droplet(n=n, r=24.0 * n / 128.0, prec="fp32")
-        s = OracleSystem(w.params, w.rho, w.n)
-        t = time.perf_counter()
-        s.step()
-        one = time.perf_counter() - t
-    for _ in range(args.warmup):
-        s.step()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        s.step()
-    dt = time.perf_counter() - t0
-    val = n ** 3 * args.steps / dt / 1e6
+    val, _, span = oracle_throughput(n, args.warmup, args.steps, procs)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "MLUPS", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * span / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "dielectric droplet, sampled at %d^3 per step (oracle)" % n},
-            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": "each step: one oracle step of the %d^3 droplet" % n},
+            "config": {"workload": "dielectric droplet, sampled at %d^3 per core per step (oracle)" % n},
+            "cpu_baseline": {"value": val, "unit": "MLUPS", "cores": procs, "kind": "oracle",
+                             "sample": "each step: one oracle step of a %d^3 droplet on each of %d cores" % (n, procs)},
             "e2e": {"value": val, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(256) k_check(const double *__restrict__ part, 
     st->mean_phi = ps / double(n);
     st->mean_phi_df = df_split(st->mean_phi);
     const double bn = st->bnorm2;
-    const double rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
+    const double rr = rel_res(r2, bn);
     st->relres = rr;
     st->zero = bn == 0.0;
     const int more = rr >= st->tol && st->iters < st->max_iter;

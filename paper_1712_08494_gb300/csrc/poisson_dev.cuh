@@ -129,6 +129,14 @@ __host__ __device__ inline DF df_split(double v) {
   return DF{h, float(v - double(h))};
 }
 
+// Relative residual sqrt(r2 / b2); zero for a vanishing right-hand side and
+// NaN when either sum is not finite (a non-finite input must not pass as a
+// vanishing right-hand side).
+__host__ __device__ inline double rel_res(double r2, double b2) {
+  if (!isfinite(r2) || !isfinite(b2)) return r2 + b2 + NAN;
+  return b2 > 0.0 ? sqrt(r2 / b2) : 0.0;
+}
+
 // Device-side solver state.
 struct PDev {
   double mean_q, mean_phi, bnorm2, rnorm2, relres, tol;
@@ -719,11 +727,11 @@ __device__ __forceinline__ void residual_site(const PArgs<T> &a, const Level<T> 
 // residual pass + fixed-order sums in every block; returns false on abort
 template <typename T, bool DFM, class Team>
 __device__ bool residual_pass(const PArgs<T> &a, const Team &tm, const Level<T> &L0, double qbar, DF qbar_df,
-                              double *sh, double &r2, double &b2, double &ps) {
+                              double *sh, double &r2, double &b2, double &ps, bool pf_always = false) {
   const long long G = tm.size();
   SumAcc<DFM> sr, sb, sp;
   const Dims d = L0.dims();
-  const bool pf = kPf && d.N >= kPfCells;
+  const bool pf = kPf && (pf_always || d.N >= kPfCells);
   Walk wp(tm.rank() + kPf * G, G, L0.nx, L0.ny);
   for (Walk w(tm.rank(), G, L0.nx, L0.ny); w.z < L0.nz; w.next(), wp.next()) {
     if (pf && wp.z < d.nz) {
@@ -820,7 +828,7 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
   const double tol = st->tol;
   const int max_iter = st->max_iter;
   const double bn = b2;
-  double rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
+  double rr = rel_res(r2, bn);
   int it = 0;
   // In the FP32 modes the level-0 residual is carried from cycle to cycle in
   // FP32 (r <- r - A e); that estimate is accurate to about 1e-5 of the
@@ -943,12 +951,12 @@ __device__ void poisson_body(const PArgs<T> &a, const Team &tm, unsigned char *s
       if (!tm.sync()) return;
       if (!residual_pass<T, DFM>(a, tm, L0, qbar, qbar_df, sh, r2, b2, ps)) return;
     }
-    rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
+    rr = rel_res(r2, bn);
     ++it;
   }
   if (exact || rr + kEstErr * rr0 < tol) break;
   if (!residual_pass<T, DFM>(a, tm, L0, qbar, qbar_df, sh, r2, b2, ps)) return;
-  rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
+  rr = rel_res(r2, bn);
   rr0 = rr;
   exact = true;
   if (rr < tol || it >= max_iter) break;

@@ -31,12 +31,18 @@ using namespace lbeh_spectral;
 namespace {
 
 constexpr int kSB = 256;  // threads per block of the spectral solve
+constexpr int kU = 8;     // elements per thread whose loads are in flight together
+// reduction of the residual one conjugate-gradient run in the compute type may
+// claim before the exact residual is formed again
+template <typename T> constexpr double kInnerReduction = 1e-4;
+template <> constexpr double kInnerReduction<double> = 0.0;
 
 template <typename T> struct AxisDev {
-  int n, nrad, W, ld;
-  int rad[kMaxStages];
-  const C2<T> *w;  // roots exp(-2 pi i t / n)
-  const T *s;      // symbol 2 (1 - cos(2 pi k / n))
+  LinePlan P;          // Stockham stages of the line length
+  int W, lgW, ld;      // lines per tile (power of two), its log2, padded line stride
+  const unsigned *code;  // butterfly codes of the plan
+  const C2<T> *tw;       // twiddles of the plan
+  const T *s;            // symbol 2 (1 - cos(2 pi k / n))
 };
 
 template <typename T> struct SArgs {
@@ -46,66 +52,136 @@ template <typename T> struct SArgs {
   Grid3 g;
   T *r, *p, *q, *e, *w;
   T inv_eref_n;  // 1 / (eps_ref N)
+  int code_cap, tw_cap;  // shared-memory capacity of the plan tables
 };
+
+// Shared memory of a block: the plan of the current pass, its tables, and
+// the two tile buffers.
+template <typename T> struct Smem {
+  LinePlan *P;
+  unsigned *code;
+  C2<T> *tw, *bA, *bB;
+};
+template <typename T> __device__ Smem<T> smem_layout(unsigned char *raw, const SArgs<T> &a, int pairs_ld) {
+  Smem<T> m;
+  m.P = reinterpret_cast<LinePlan *>(raw);
+  size_t off = (sizeof(LinePlan) + 15) & ~size_t(15);
+  m.code = reinterpret_cast<unsigned *>(raw + off);
+  off += ((size_t)a.code_cap * 4 + 15) & ~size_t(15);
+  m.tw = reinterpret_cast<C2<T> *>(raw + off);
+  off += ((size_t)a.tw_cap * sizeof(C2<T>) + 15) & ~size_t(15);
+  m.bA = reinterpret_cast<C2<T> *>(raw + off);
+  m.bB = m.bA + pairs_ld;
+  return m;
+}
 
 // One lattice pass along axis A over every tile owned by this block: stage
 // the tile through `load`, transform each pair of lines (forward; with `fuse`
 // also the symbol scaling and the second transform), write through `store`.
+// Element positions advance without integer division: for the x pass a
+// thread's (line, position) steps by the block size decomposed once; for the
+// y and z passes the tile width W divides the block size, so each thread
+// keeps its line and steps its position.
 template <typename T, class Load, class Store>
-__device__ void tile_pass(const SArgs<T> &a, int A, bool fuse, C2<T> *buf, Load load, Store store) {
-  const AxisDev<T> P = a.ax[A];
+__device__ void tile_pass(const SArgs<T> &a, int A, bool fuse, unsigned char *raw, Load load, Store store) {
+  const AxisDev<T> &X = a.ax[A];
   const Grid3 g = a.g;
-  const int N = P.n, W = P.W, pairs = W >> 1, ld = P.ld;
-  C2<T> *bA = buf, *bB = buf + pairs * ld;
+  const int W = X.W, lgW = X.lgW, pairs = W >> 1, ld = X.ld;
+  const Smem<T> sm = smem_layout<T>(raw, a, pairs * ld);
+  // plan of this pass into shared memory
+  if (threadIdx.x == 0) *sm.P = X.P;
+  for (int k = threadIdx.x; k < X.P.ncode; k += blockDim.x) sm.code[k] = X.code[k];
+  for (int k = threadIdx.x; k < X.P.ntw; k += blockDim.x) sm.tw[k] = X.tw[k];
+  __syncthreads();
+  const LinePlan &P = *sm.P;
+  const int N = P.n;
   const int nt = tile_count(g, A, W);
+  const int xt = (g.nx + W - 1) >> lgW;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int nm = warp < pairs ? (pairs - warp + nw - 1) / nw : 0;  // line pairs of this warp
+  const int B = blockDim.x;
+  // x pass: (line, position) of element tid and the block stride, decomposed once
+  const int l0 = threadIdx.x / N, p0 = threadIdx.x - (threadIdx.x / N) * N;
+  const int dl = B / N, dp = B - (B / N) * N;
+  const long long nlines = (long long)g.ny * g.nz;
+  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
-    for (int el = threadIdx.x; el < W * N; el += blockDim.x) {
-      int l, pos;
-      if (A == 0) {  // consecutive threads along the row
-        l = el / N;
-        pos = el - l * N;
-      } else {  // consecutive threads along x
-        pos = el / W;
-        l = el - pos * W;
+    // tile origin: first row (x pass) or (x0, o) with o = z (y pass) or y (z pass)
+    const int o = A == 0 ? 0 : t / xt;
+    const int x0 = A == 0 ? 0 : (t - o * xt) << lgW;
+    const long long row0 = (long long)t << lgW;
+    // staging in chunks of kU elements per thread: all loads of a chunk are
+    // issued before the first shared-memory store (latency hiding)
+    if (A == 0) {
+      int l = l0, pos = p0;
+      for (int el0 = threadIdx.x; el0 < W * N; el0 += kU * B) {
+        T v[kU];
+        int ls[kU], ps[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          ls[u] = l;
+          ps[u] = pos;
+          const long long row = row0 + l;
+          v[u] = (el0 + u * B < W * N && row < nlines) ? load(row * sy + pos) : T(0);
+          pos += dp;
+          l += dl;
+          if (pos >= N) {
+            pos -= N;
+            ++l;
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+          if (el0 + u * B < W * N) reinterpret_cast<T *>(sm.bA + (ls[u] >> 1) * ld + ps[u])[ls[u] & 1] = v[u];
       }
-      bool ok;
-      const long long gi = tile_index(g, A, W, t, l, pos, ok);
-      reinterpret_cast<T *>(bA + (l >> 1) * ld + pos)[l & 1] = ok ? load(gi) : T(0);
+    } else {
+      const int l = threadIdx.x & (W - 1);
+      const bool ok = x0 + l < g.nx;
+      const long long base = A == 1 ? (long long)o * sz + x0 + l : (long long)o * sy + x0 + l;
+      const long long step = A == 1 ? sy : sz;
+      const int pstep = B >> lgW;
+      T *col = reinterpret_cast<T *>(sm.bA + (l >> 1) * ld) + (l & 1);
+      for (int q0 = threadIdx.x >> lgW; q0 < N; q0 += kU * pstep) {
+        T v[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int pos = q0 + u * pstep;
+          v[u] = (ok && pos < N) ? load(base + pos * step) : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+          const int pos = q0 + u * pstep;
+          if (pos < N) col[2 * pos] = v[u];
+        }
+      }
     }
     __syncthreads();
-    C2<T> *in = bA, *out = bB;
+    C2<T> *in = sm.bA, *out = sm.bB;
     for (int rep = 0; rep < (fuse ? 2 : 1); ++rep) {
-      int Ns = 1;
-      for (int s = 0; s < P.nrad; ++s) {
-        const int R = P.rad[s], nb = N / R;
-        for (int j = lane; j < nm * nb; j += 32) {
-          const int mi = j / nb, jj = j - mi * nb;
+      for (int s = 0; s < P.nst; ++s) {
+        const int nb = P.nb[s];
+        for (int mi = 0; mi < nm; ++mi) {
           const int m = warp + mi * nw;
-          stage_bfly(in + m * ld, out + m * ld, P.w, N, R, Ns, jj);
+          for (int j = lane; j < nb; j += 32) plan_bfly(P, s, sm.code, sm.tw, in + m * ld, out + m * ld, j);
         }
         __syncwarp();
-        Ns *= R;
         C2<T> *tp = in;
         in = out;
         out = tp;
       }
       if (fuse && rep == 0) {
         // Hartley values of both lines, times the inverse symbol, packed again
+        const T *sx = a.ax[0].s, *sy_ = a.ax[1].s, *sz_ = a.ax[2].s;
         for (int mi = 0; mi < nm; ++mi) {
           const int m = warp + mi * nw;
-          int kxa, kxb, ky;
-          zline_k(g, W, t, 2 * m, kxa, ky);
-          zline_k(g, W, t, 2 * m + 1, kxb, ky);
+          const int kxa = x0 + 2 * m, kxb = kxa + 1, ky = o;
           for (int k = lane; k <= N / 2; k += 32) {
             const Split<T> sp = pair_split(in + m * ld, N, k);
             const int kn = k == 0 ? 0 : N - k;
-            const T *sx = a.ax[0].s, *sy = a.ax[1].s, *sz = a.ax[2].s;
-            const T sa = kxa < g.nx ? inv_symbol(kxa, ky, k, sx, sy, sz, a.inv_eref_n) : T(0);
-            const T sb = kxb < g.nx ? inv_symbol(kxb, ky, k, sx, sy, sz, a.inv_eref_n) : T(0);
-            const T sa2 = kxa < g.nx ? inv_symbol(kxa, ky, kn, sx, sy, sz, a.inv_eref_n) : T(0);
-            const T sb2 = kxb < g.nx ? inv_symbol(kxb, ky, kn, sx, sy, sz, a.inv_eref_n) : T(0);
+            const T sa = kxa < g.nx ? inv_symbol(kxa, ky, k, sx, sy_, sz_, a.inv_eref_n) : T(0);
+            const T sb = kxb < g.nx ? inv_symbol(kxb, ky, k, sx, sy_, sz_, a.inv_eref_n) : T(0);
+            const T sa2 = kxa < g.nx ? inv_symbol(kxa, ky, kn, sx, sy_, sz_, a.inv_eref_n) : T(0);
+            const T sb2 = kxb < g.nx ? inv_symbol(kxb, ky, kn, sx, sy_, sz_, a.inv_eref_n) : T(0);
             out[m * ld + k] = C2<T>{sp.ak * sa, sp.bk * sb};
             out[m * ld + kn] = C2<T>{sp.an * sa2, sp.bn * sb2};
           }
@@ -117,20 +193,30 @@ __device__ void tile_pass(const SArgs<T> &a, int A, bool fuse, C2<T> *buf, Load 
       }
     }
     __syncthreads();
-    for (int el = threadIdx.x; el < W * N; el += blockDim.x) {
-      int l, pos;
-      if (A == 0) {
-        l = el / N;
-        pos = el - l * N;
-      } else {
-        pos = el / W;
-        l = el - pos * W;
+    if (A == 0) {
+      int l = l0, pos = p0;
+      for (int el = threadIdx.x; el < W * N; el += B) {
+        const long long row = row0 + l;
+        if (row < nlines) {
+          const Split<T> sp = pair_split(in + (l >> 1) * ld, N, pos);
+          store(row * sy + pos, (l & 1) ? sp.bk : sp.ak);
+        }
+        pos += dp;
+        l += dl;
+        if (pos >= N) {
+          pos -= N;
+          ++l;
+        }
       }
-      bool ok;
-      const long long gi = tile_index(g, A, W, t, l, pos, ok);
-      if (ok) {
-        const Split<T> sp = pair_split(in + (l >> 1) * ld, N, pos);
-        store(gi, (l & 1) ? sp.bk : sp.ak);
+    } else {
+      const int l = threadIdx.x & (W - 1);
+      if (x0 + l < g.nx) {
+        const long long base = A == 1 ? (long long)o * sz + x0 + l : (long long)o * sy + x0 + l;
+        const long long step = A == 1 ? sy : sz;
+        for (int pos = threadIdx.x >> lgW; pos < N; pos += B >> lgW) {
+          const Split<T> sp = pair_split(in + (l >> 1) * ld, N, pos);
+          store(base + pos * step, (l & 1) ? sp.bk : sp.ak);
+        }
       }
     }
     __syncthreads();
@@ -144,27 +230,53 @@ __device__ double matvec_update(const SArgs<T> &a, const T *z, T beta, bool firs
   const Level<T> L0 = a.L0;
   const Dims d = L0.dims();
   const long long G = (long long)gridDim.x * blockDim.x;
+  constexpr int U = 2;  // cells per thread with their loads in flight together
   SumAcc<DFM> acc;
-  for (Walk wk(blockIdx.x * (long long)blockDim.x + threadIdx.x, G, d.nx, d.ny); wk.z < d.nz; wk.next()) {
-    const Nbr c = nbr(d, wk.u, wk.y, wk.z);
-    const Faces<T> f = faces(L0, c.i, c.xp, c.xm, c.yp, c.ym, c.zp, c.zm);
-    const T zi = z[c.i];
-    const T Az = f.xp * (z[c.xp] - zi) + f.xm * (z[c.xm] - zi) + f.yp * (z[c.yp] - zi) + f.ym * (z[c.ym] - zi) +
-                 f.zp * (z[c.zp] - zi) + f.zm * (z[c.zm] - zi);
-    const T pn = first ? zi : zi + beta * a.p[c.i];
-    const T qn = first ? Az : Az + beta * a.q[c.i];
-    a.p[c.i] = pn;
-    a.q[c.i] = qn;
-    acc.add(pn * qn);
+  Walk wk(blockIdx.x * (long long)blockDim.x + threadIdx.x, G, d.nx, d.ny);
+  while (wk.z < d.nz) {
+    Nbr c[U];
+    bool v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v[u] = wk.z < d.nz;
+      c[u] = nbr(d, v[u] ? wk.u : 0, v[u] ? wk.y : 0, v[u] ? wk.z : 0);
+      if (v[u]) wk.next();
+    }
+    T zc[U], zn[U][6], ec[U], en[U][6], pv[U], qv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const unsigned nb6[6] = {c[u].xp, c[u].xm, c[u].yp, c[u].ym, c[u].zp, c[u].zm};
+      zc[u] = z[c[u].i];
+      ec[u] = L0.eps[c[u].i];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        zn[u][k] = z[nb6[k]];
+        en[u][k] = L0.eps[nb6[k]];
+      }
+      pv[u] = first ? T(0) : a.p[c[u].i];
+      qv[u] = first ? T(0) : a.q[c[u].i];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!v[u]) continue;
+      T Az = T(0);
+#pragma unroll
+      for (int k = 0; k < 6; ++k) Az += T(0.5) * (ec[u] + en[u][k]) * (zn[u][k] - zc[u]);
+      const T pn = zc[u] + beta * pv[u];
+      const T qn = Az + beta * qv[u];
+      a.p[c[u].i] = pn;
+      a.q[c[u].i] = qn;
+      acc.add(pn * qn);
+    }
   }
   return block_sum_n(acc.get(), sh);
 }
 
 template <typename T, bool DFM>
-__global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
+__global__ void __launch_bounds__(kSB, sizeof(T) == 4 ? 3 : 2) k_spectral(SArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[kSB];
-  C2<T> *buf = reinterpret_cast<C2<T> *>(smem_raw);
+  unsigned char *buf = smem_raw;
   const PArgs<T> &pa = a.pa;
   const GridTeam tm{pa.bar, pa.status, pa.spin_limit};
   const Level<T> L0 = a.L0;
@@ -175,24 +287,53 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   PDev *st = pa.st;
   const int have_prev = st->have_prev;
 
-  // initial guess 2 phi(t-1) - phi(t-2), sum of q
+  // initial guess 2 phi(t-1) - phi(t-2), sum of q (kU cells per thread in flight)
   SumAcc<DFM> sq;
-  for (long long i = gt; i < N; i += G) {
+  for (long long i0 = gt; i0 < N; i0 += kU * G) {
     if constexpr (DFM) {
-      const DF pv{pa.phi_hi[i], pa.phi_lo[i]};
-      if (have_prev) {
-        const DF gv = df_sub(DF{2.f * pv.hi, 2.f * pv.lo}, DF{pa.prev_hi[i], pa.prev_lo[i]});
-        pa.phi_hi[i] = gv.hi;
-        pa.phi_lo[i] = gv.lo;
+      float h[kU], l[kU], ph[kU], pl[kU], qq[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long i = i0 + u * G;
+        const bool in = i < N;
+        h[u] = in ? pa.phi_hi[i] : 0.f;
+        l[u] = in ? pa.phi_lo[i] : 0.f;
+        ph[u] = in && have_prev ? pa.prev_hi[i] : 0.f;
+        pl[u] = in && have_prev ? pa.prev_lo[i] : 0.f;
+        qq[u] = in ? float(pa.q[i]) : 0.f;
       }
-      pa.prev_hi[i] = pv.hi;
-      pa.prev_lo[i] = pv.lo;
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long i = i0 + u * G;
+        if (i >= N) continue;
+        if (have_prev) {
+          const DF gv = df_sub(DF{2.f * h[u], 2.f * l[u]}, DF{ph[u], pl[u]});
+          pa.phi_hi[i] = gv.hi;
+          pa.phi_lo[i] = gv.lo;
+        }
+        pa.prev_hi[i] = h[u];
+        pa.prev_lo[i] = l[u];
+        sq.add(qq[u]);
+      }
     } else {
-      const double pv = pa.phi[i];
-      if (have_prev) pa.phi[i] = 2.0 * pv - pa.prev[i];
-      pa.prev[i] = pv;
+      double pv[kU], pr[kU], qq[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long i = i0 + u * G;
+        const bool in = i < N;
+        pv[u] = in ? pa.phi[i] : 0.0;
+        pr[u] = in && have_prev ? pa.prev[i] : 0.0;
+        qq[u] = in ? double(pa.q[i]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long i = i0 + u * G;
+        if (i >= N) continue;
+        if (have_prev) pa.phi[i] = 2.0 * pv[u] - pr[u];
+        pa.prev[i] = pv[u];
+        sq.add(qq[u]);
+      }
     }
-    sq.add(pa.q[i]);
   }
   {
     const double v = block_sum_n(sq.get(), sh);
@@ -211,14 +352,18 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   for (int outer = 0;; ++outer) {
     // exact residual r = b - A phi (FP64 / double-float), |r|^2, |b|^2, sum phi
     double r2, b2, ps;
-    if (!residual_pass<T, DFM>(pa, tm, L0, qbar, qbar_df, sh, r2, b2, ps)) return;
+    // (L2 prefetch hints: the potential and eps come from DRAM after the step's other kernels)
+    if (!residual_pass<T, DFM>(pa, tm, L0, qbar, qbar_df, sh, r2, b2, ps, true)) return;
     if (outer == 0) bn = b2;
-    rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
+    rr = rel_res(r2, bn);
     exact = true;
     shift = ps / double(N);
     have_e = false;
     if (rr < tol || it >= max_iter || !isfinite(rr)) break;
     const double rr_start = rr;
+    // the compute-type recursion tracks the residual to a fraction of its
+    // start; below that the exact residual restarts the iteration
+    const double target = fmax(tol, rr_start * kInnerReduction<T>);
     // conjugate gradients on A e = r
     double rho_old = 1.0, alpha = 0.0, sum_e = 0.0;
     bool first = true;
@@ -256,9 +401,9 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
       if (have_e) sum_e = sum_partials(pa.part + nb, nb, sh);
       if (upd) {
         ++it;
-        rr = bn > 0.0 ? sqrt(r2 / bn) : 0.0;
+        rr = rel_res(r2, bn);
         exact = false;
-        if (rr < tol || it >= max_iter || !isfinite(rr)) break;
+        if (rr < target || it >= max_iter || !isfinite(rr)) break;
       }
       // preconditioner: Y, Z (scale), Y, X passes on w
       tile_pass<T>(
@@ -314,18 +459,40 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   // phi += e (when pending), mean-free
   const bool zero = bn == 0.0;
   const DF shift_df = df_split(shift);
-  for (long long i = gt; i < N; i += G) {
+  for (long long i0 = gt; i0 < N; i0 += kU * G) {
     if constexpr (DFM) {
-      DF v{0.f, 0.f};
-      if (!zero) {
-        v = DF{pa.phi_hi[i], pa.phi_lo[i]};
-        if (have_e) v = df_add(v, DF{float(a.e[i]), 0.f});
-        v = df_sub(v, shift_df);
+      float h[kU], l[kU], ev[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long i = i0 + u * G;
+        const bool in = i < N && !zero;
+        h[u] = in ? pa.phi_hi[i] : 0.f;
+        l[u] = in ? pa.phi_lo[i] : 0.f;
+        ev[u] = in && have_e ? float(a.e[i]) : 0.f;
       }
-      pa.phi_hi[i] = v.hi;
-      pa.phi_lo[i] = v.lo;
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long i = i0 + u * G;
+        if (i >= N) continue;
+        DF v{0.f, 0.f};
+        if (!zero) v = df_sub(df_add(DF{h[u], l[u]}, DF{ev[u], 0.f}), shift_df);
+        pa.phi_hi[i] = v.hi;
+        pa.phi_lo[i] = v.lo;
+      }
     } else {
-      pa.phi[i] = zero ? 0.0 : pa.phi[i] + (have_e ? double(a.e[i]) : 0.0) - shift;
+      double pv[kU], ev[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long i = i0 + u * G;
+        const bool in = i < N && !zero;
+        pv[u] = in ? pa.phi[i] : 0.0;
+        ev[u] = in && have_e ? double(a.e[i]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long i = i0 + u * G;
+        if (i < N) pa.phi[i] = zero ? 0.0 : pv[u] + ev[u] - shift;
+      }
     }
   }
   if (gt == 0) {
@@ -346,15 +513,6 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   (void)exact;
 }
 
-template <typename T> std::vector<C2<T>> roots_of(int n) {
-  std::vector<C2<T>> w(n);
-  for (int t = 0; t < n; ++t) {
-    const double ang = -2.0 * M_PI * double(t) / double(n);
-    w[t] = C2<T>{T(std::cos(ang)), T(std::sin(ang))};
-  }
-  return w;
-}
-
 }  // namespace
 
 struct Spectral {
@@ -363,9 +521,11 @@ struct Spectral {
   size_t smem = 0;
   std::vector<void *> allocs;
   void *r = nullptr, *p = nullptr, *q = nullptr, *e = nullptr, *w = nullptr;
-  void *tw[3] = {nullptr, nullptr, nullptr}, *sym[3] = {nullptr, nullptr, nullptr};
-  int n[3] = {0, 0, 0}, W[3] = {0, 0, 0}, nrad[3] = {0, 0, 0};
-  int rad[3][kMaxStages] = {};
+  void *code[3] = {nullptr, nullptr, nullptr}, *tw[3] = {nullptr, nullptr, nullptr};
+  void *sym[3] = {nullptr, nullptr, nullptr};
+  LinePlan plan[3];
+  int W[3] = {0, 0, 0}, lgW[3] = {0, 0, 0};
+  int code_cap = 0, tw_cap = 0;
   double eps_ref = 1.0;
 };
 
@@ -373,7 +533,7 @@ bool spectral_supported(const Dims &d, int fp64) {
   int rad[kMaxStages];
   const int lim = fp64 ? 256 : kMaxN;
   for (int n : {d.nx, d.ny, d.nz})
-    if (n < 2 || n > lim || !factorize(n, rad)) return false;
+    if (n < 2 || n > lim || !plan_radices(n, rad)) return false;
   return true;
 }
 
@@ -388,23 +548,37 @@ template <typename T> static bool spectral_setup(Spectral *s, const Dims &d) {
   if (!(s->r = dal(nb)) || !(s->p = dal(nb)) || !(s->q = dal(nb)) || !(s->e = dal(nb)) || !(s->w = dal(nb)))
     return false;
   const int ns[3] = {d.nx, d.ny, d.nz};
-  size_t smem = 0;
+  size_t tiles = 0;
   for (int A = 0; A < 3; ++A) {
     const int n = ns[A];
-    s->n[A] = n;
-    s->nrad[A] = factorize(n, s->rad[A]);
-    int W = 32;  // lines per tile: the largest of 32, 16, 8 whose tile fits 40 KB
-    while (W > 8 && 2 * (W / 2) * (n + 1) * sizeof(C2<T>) > 40 * 1024) W /= 2;
+    std::vector<unsigned> code;
+    std::vector<C2<double>> twd;
+    if (!build_plan(n, s->plan[A], code, twd)) return false;
+    std::vector<C2<T>> tw(twd.size());
+    for (size_t k = 0; k < twd.size(); ++k) tw[k] = C2<T>{T(twd[k].x), T(twd[k].y)};
+    s->code_cap = std::max(s->code_cap, (int)code.size());
+    s->tw_cap = std::max(s->tw_cap, (int)tw.size());
+    int W = 32, lg = 5;  // lines per tile: the largest of 32, 16, 8 whose tile fits 40 KB
+    while (W > 8 && 2 * (W / 2) * (n + 1) * sizeof(C2<T>) > 40 * 1024) {
+      W /= 2;
+      --lg;
+    }
     s->W[A] = W;
-    smem = std::max(smem, 2 * (size_t)(W / 2) * (n + 1) * sizeof(C2<T>));
-    std::vector<C2<T>> w = roots_of<T>(n);
+    s->lgW[A] = lg;
+    tiles = std::max(tiles, 2 * (size_t)(W / 2) * (n + 1) * sizeof(C2<T>));
     std::vector<T> sy(n);
     for (int k = 0; k < n; ++k) sy[k] = T(2.0 * (1.0 - std::cos(2.0 * M_PI * double(k) / double(n))));
-    if (!(s->tw[A] = dal(sizeof(C2<T>) * n)) || !(s->sym[A] = dal(sizeof(T) * n))) return false;
-    if (cudaMemcpy(s->tw[A], w.data(), sizeof(C2<T>) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+    if (!(s->code[A] = dal(4 * code.size())) || !(s->tw[A] = dal(sizeof(C2<T>) * tw.size())) ||
+        !(s->sym[A] = dal(sizeof(T) * n)))
+      return false;
+    if (cudaMemcpy(s->code[A], code.data(), 4 * code.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(s->tw[A], tw.data(), sizeof(C2<T>) * tw.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(s->sym[A], sy.data(), sizeof(T) * n, cudaMemcpyHostToDevice) != cudaSuccess)
       return false;
   }
+  // layout of smem_layout(): plan, codes, twiddles, tile buffers (16-byte aligned parts)
+  auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
+  const size_t smem = al(sizeof(LinePlan)) + al((size_t)s->code_cap * 4) + al((size_t)s->tw_cap * sizeof(C2<T>)) + tiles;
   s->smem = smem;
   constexpr bool DFM = std::is_same<T, float>::value;
   if (!raise_smem_limit((const void *)k_spectral<T, DFM>, smem)) return false;
@@ -452,15 +626,17 @@ template <typename T, bool DFM> static int launch(Spectral *s, const Ctx &c, con
   L0.b = (T *)s->r;
   a.L0 = L0;
   for (int A = 0; A < 3; ++A) {
-    AxisDev<T> &P = a.ax[A];
-    P.n = s->n[A];
-    P.nrad = s->nrad[A];
-    P.W = s->W[A];
-    P.ld = s->n[A] + 1;
-    for (int k = 0; k < kMaxStages; ++k) P.rad[k] = s->rad[A][k];
-    P.w = (const C2<T> *)s->tw[A];
-    P.s = (const T *)s->sym[A];
+    AxisDev<T> &X = a.ax[A];
+    X.P = s->plan[A];
+    X.W = s->W[A];
+    X.lgW = s->lgW[A];
+    X.ld = s->plan[A].n + 1;
+    X.code = (const unsigned *)s->code[A];
+    X.tw = (const C2<T> *)s->tw[A];
+    X.s = (const T *)s->sym[A];
   }
+  a.code_cap = s->code_cap;
+  a.tw_cap = s->tw_cap;
   a.g = Grid3{c.d.nx, c.d.ny, c.d.nz};
   a.r = (T *)s->r;
   a.p = (T *)s->p;

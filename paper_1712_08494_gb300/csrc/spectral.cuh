@@ -24,6 +24,7 @@
 // The line and tile functions are __host__ __device__: the tests run them on
 // the host with the same index arithmetic as the device solver.
 #pragma once
+#include <cmath>
 #ifndef LBEH_SPEC_HD
 #ifdef __CUDACC__
 #define LBEH_SPEC_HD __host__ __device__ __forceinline__
@@ -133,6 +134,102 @@ LBEH_SPEC_HD void stage_bfly(const C2<T> *in, C2<T> *out, const C2<T> *w, int N,
     case 5: stage_bfly_r<T, 5>(in, out, w, N, Ns, j); break;
     case 7: stage_bfly_r<T, 7>(in, out, w, N, Ns, j); break;
     default: stage_bfly_r<T, 8>(in, out, w, N, Ns, j); break;
+  }
+}
+
+// ---------------------------------------------------------------- line plans
+// Precomputed Stockham stages of one line length, so that a butterfly needs
+// no integer division: for stage s with radix R after sub-transforms of size
+// Ns, butterfly j (0 <= j < N/R) reads in[j + r N/R] and writes
+// out[base_j + a Ns]; code[j] packs base_j (low 16 bits) and the offset of its
+// R - 1 twiddles in the stage's twiddle table (high 16 bits).  After the
+// twiddles of a stage with a generic radix (3, 5, 7) come its R roots of unity
+// exp(-2 pi i t / R).  Radices: 8 while at least 32 butterflies remain per
+// stage, then 4, 2, 3, 5, 7.
+struct LinePlan {
+  int n, nst, ncode, ntw;
+  int R[kMaxStages], Ns[kMaxStages], nb[kMaxStages], code_off[kMaxStages], tw_off[kMaxStages];
+};
+
+LBEH_SPEC_HD int plan_radices(int N, int *rad) {
+  if (N < 1 || N > kMaxN) return 0;
+  int m = 0, n = N;
+  while (n % 8 == 0 && N / 8 >= 32 && m < kMaxStages) {
+    rad[m++] = 8;
+    n /= 8;
+  }
+  const int order[5] = {4, 2, 3, 5, 7};
+  for (int t = 0; t < 5; ++t)
+    while (n % order[t] == 0 && m < kMaxStages) {
+      rad[m++] = order[t];
+      n /= order[t];
+    }
+  return n == 1 ? m : 0;
+}
+
+// host: the plan and its tables in FP64 (converted to the compute type by the caller)
+template <class CodeVec, class TwVec> inline bool build_plan(int N, LinePlan &P, CodeVec &code, TwVec &tw) {
+  int rad[kMaxStages];
+  const int m = plan_radices(N, rad);
+  if (!m) return false;
+  P.n = N;
+  P.nst = m;
+  code.clear();
+  tw.clear();
+  const double two_pi = 6.283185307179586476925286766559;
+  int Ns = 1;
+  for (int s = 0; s < m; ++s) {
+    const int R = rad[s], nb = N / R;
+    P.R[s] = R;
+    P.Ns[s] = Ns;
+    P.nb[s] = nb;
+    P.code_off[s] = (int)code.size();
+    P.tw_off[s] = (int)tw.size();
+    for (int jn = 0; jn < Ns; ++jn)
+      for (int r = 1; r < R; ++r) {
+        const double a = -two_pi * double(jn * r) / double(Ns * R);
+        tw.push_back({std::cos(a), std::sin(a)});
+      }
+    if (R == 3 || R == 5 || R == 7)
+      for (int t = 0; t < R; ++t) {
+        const double a = -two_pi * double(t) / double(R);
+        tw.push_back({std::cos(a), std::sin(a)});
+      }
+    for (int j = 0; j < nb; ++j) {
+      const int jn = j % Ns;
+      const unsigned base = unsigned((j / Ns) * Ns * R + jn);
+      code.push_back(base | (unsigned(jn * (R - 1)) << 16));
+    }
+    Ns *= R;
+  }
+  P.ncode = (int)code.size();
+  P.ntw = (int)tw.size();
+  return true;
+}
+
+// butterfly j of stage s (tables of this stage: code + code_off, tw + tw_off)
+template <typename T, int R>
+LBEH_SPEC_HD void plan_bfly_r(const C2<T> *in, C2<T> *out, const C2<T> *tw, int Ns, int nb, int j, unsigned code) {
+  C2<T> v[R];
+  const unsigned base = code & 0xFFFFu, tb = code >> 16;
+  v[0] = in[j];
+  for (int r = 1; r < R; ++r) v[r] = cmul(in[j + r * nb], tw[tb + r - 1]);
+  Dft<T, R>::run(v, tw + Ns * (R - 1), 1);
+  for (int a = 0; a < R; ++a) out[base + a * Ns] = v[a];
+}
+template <typename T>
+LBEH_SPEC_HD void plan_bfly(const LinePlan &P, int s, const unsigned *code, const C2<T> *tw, const C2<T> *in,
+                            C2<T> *out, int j) {
+  const int Ns = P.Ns[s], nb = P.nb[s];
+  const unsigned c = code[P.code_off[s] + j];
+  const C2<T> *t = tw + P.tw_off[s];
+  switch (P.R[s]) {
+    case 2: plan_bfly_r<T, 2>(in, out, t, Ns, nb, j, c); break;
+    case 3: plan_bfly_r<T, 3>(in, out, t, Ns, nb, j, c); break;
+    case 4: plan_bfly_r<T, 4>(in, out, t, Ns, nb, j, c); break;
+    case 5: plan_bfly_r<T, 5>(in, out, t, Ns, nb, j, c); break;
+    case 7: plan_bfly_r<T, 7>(in, out, t, Ns, nb, j, c); break;
+    default: plan_bfly_r<T, 8>(in, out, t, Ns, nb, j, c); break;
   }
 }
 

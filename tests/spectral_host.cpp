@@ -23,10 +23,30 @@ template <typename T> static std::vector<T> symb(int n) {
   return c;
 }
 
+// the Stockham stages of a line plan (the device solver's transform)
 template <typename T>
-static void pass_host(T *u, const Grid3 &g, int A, int W, const std::vector<C2<T>> &w, bool fuse, T inv_n,
+static C2<T> *fft_plan(C2<T> *b0, C2<T> *b1, const LinePlan &P, const std::vector<unsigned> &code,
+                       const std::vector<C2<T>> &tw) {
+  C2<T> *in = b0, *out = b1;
+  for (int s = 0; s < P.nst; ++s) {
+    for (int j = 0; j < P.nb[s]; ++j) plan_bfly(P, s, code.data(), tw.data(), in, out, j);
+    C2<T> *t = in;
+    in = out;
+    out = t;
+  }
+  return in;
+}
+
+template <typename T>
+static void pass_host(T *u, const Grid3 &g, int A, int W, const std::vector<C2<T>> &, bool fuse, T inv_n,
                       const T *sx, const T *sy, const T *sz) {
   const int N = line_len(g, A);
+  LinePlan P;
+  std::vector<unsigned> code;
+  std::vector<C2<double>> twd;
+  build_plan(N, P, code, twd);
+  std::vector<C2<T>> tw(twd.size());
+  for (size_t k = 0; k < twd.size(); ++k) tw[k] = C2<T>{T(twd[k].x), T(twd[k].y)};
   const int pairs = W / 2;
   std::vector<C2<T>> b0(N), b1(N), Z((size_t)pairs * N);
   const int nt = tile_count(g, A, W);
@@ -38,7 +58,7 @@ static void pass_host(T *u, const Grid3 &g, int A, int W, const std::vector<C2<T
         const long long ib = tile_index(g, A, W, t, 2 * m + 1, p, ob);
         b0[p] = C2<T>{oa ? u[ia] : T(0), ob ? u[ib] : T(0)};
       }
-      C2<T> *r = fft_host(b0.data(), b1.data(), N, w.data());
+      C2<T> *r = fft_plan(b0.data(), b1.data(), P, code, tw);
       if (fuse) {
         int kxa, kxb, ky;
         zline_k(g, W, t, 2 * m, kxa, ky);
@@ -56,7 +76,7 @@ static void pass_host(T *u, const Grid3 &g, int A, int W, const std::vector<C2<T
         }
         C2<T> *o = r == b0.data() ? b1.data() : b0.data();
         for (int k = 0; k < N; ++k) o[k] = zz[k];
-        r = fft_host(o, r, N, w.data());
+        r = fft_plan(o, r, P, code, tw);
       }
       for (int p = 0; p < N; ++p) Z[(size_t)m * N + p] = r[p];
     }

@@ -1,0 +1,127 @@
+"""Long-run parity at the workloads' own settings, against the FP64 oracle.
+
+* Plain method, 32^3, the whole 200 steps: the FP32 path (double-float
+  potential, FP32 populations) against the oracle run of the same input,
+  per field: densities, ion concentrations, potential and physical velocity.
+* Dielectric droplet, 64^3 copy of the 128^3 workload (drop radius 12, seed
+  1, E_z = 1e-3), 500 steps, FP32 and BF16 population storage: the drop
+  deformation every 25 steps and, at step 500, the densities, ions, potential
+  and velocity at 2048 seeded sites, against the oracle trajectory written by
+  tests/golden/make_parity_runs.py (oracle only, Poisson residual 1e-10).
+* Electrophoresis suspension, 64^3 subset of the 256^3 workload (3 moving
+  spheres of radius 6 at the same number density, seed 2, E_x = 1e-3), FP32
+  and BF16: colloid velocities every 10 steps and the mean drift velocity
+  over the second half of the stored run, against the oracle trajectory of
+  the same script.
+
+Tolerances are relative to the field's maximum (velocities: to the maximum
+speed of the stored trajectory) and were set from measured errors with a
+margin; they are stated beside each assertion.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from _common import gpu_for, oracle_for, rel_err
+from oracle import observables
+
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+@pytest.fixture(scope="module")
+def plain32_oracle():
+    w = synth.two_slab(nx=32, ny=32, nz=32, G=4.0, prec="fp64", tol=1e-10)
+    w.params.poisson_max_iter = 400
+    so = oracle_for(w)
+    for _ in range(200):
+        so.step()
+        assert so.poisson_relres < so.tol
+    return w, so
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_plain_method_32_cubed_200_steps(lbeh, plain32_oracle, prec):
+    w, so = plain32_oracle
+    wg = synth.two_slab(nx=32, ny=32, nz=32, G=4.0, prec=prec, tol=1e-10)
+    wg.params.poisson_max_iter = 400
+    sg = gpu_for(wg, lbeh)
+    for _ in range(200):
+        assert sg.step(1) == lbeh.LBEH_OK
+    g = sg.get(("rho", "n", "phi", "u"))
+    err = {"rho": max(rel_err(g["rho"][s], so.densities()[s]) for s in range(2)),
+           "n": max(rel_err(g["n"][s], so.n[s]) for s in range(2)),
+           "phi": rel_err(g["phi"], so.phi), "u": rel_err(g["u"], so.last_u)}
+    print("plain32", prec, err)
+    if prec == "fp64":
+        assert err["rho"] < 1e-10 and err["n"] < 1e-10 and err["phi"] < 1e-8 and err["u"] < 1e-8, err
+    else:
+        # FP32 storage and arithmetic over 200 steps (2^-24 per rounding)
+        assert err["rho"] < 2e-5 and err["n"] < 5e-5 and err["phi"] < 5e-4 and err["u"] < 5e-3, err
+    sg.close()
+
+
+def _golden(name):
+    p = os.path.join(GOLDEN, name)
+    if not os.path.exists(p):
+        pytest.skip("oracle trajectory %s not written" % name)
+    return np.load(p)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_droplet_64_copy_500_steps_against_oracle(lbeh, prec):
+    gold = _golden("parity_droplet64.npz")
+    steps, every = int(gold["steps"]), int(gold["every"])
+    w = synth.droplet(n=64, r=12.0, prec=prec, seed=1, salt=1e-3, Ez=1e-3)
+    sg = gpu_for(w, lbeh)
+    D = [sg.observables().deformation]
+    for _ in range(steps // every):
+        assert sg.step(every) == lbeh.LBEH_OK
+        D.append(sg.observables().deformation)
+    D = np.array(D)
+    dD = np.abs(D - gold["deformation"]).max()
+    g = sg.get(("rho", "n", "phi", "u"))
+    idx = gold["idx"]
+    err = {"rho": max(float(np.abs(g["rho"][s].reshape(-1)[idx] - gold["rho"][s]).max() / gold["max_rho"][s])
+                      for s in range(2)),
+           "n": max(float(np.abs(g["n"][s].reshape(-1)[idx] - gold["n"][s]).max() / gold["max_n"][s])
+                    for s in range(2)),
+           "phi": float(np.abs(g["phi"].reshape(-1)[idx] - gold["phi"]).max() / gold["max_phi"]),
+           "u": float(np.abs(np.asarray(g["u"]).reshape(3, -1)[:, idx] - gold["u"]).max() / gold["max_u"]),
+           "deformation_abs": float(dD), "deformation_scale": float(np.abs(gold["deformation"]).max())}
+    print("droplet64", prec, err)
+    if prec == "fp32":
+        assert err["rho"] < 1e-4 and err["n"] < 1e-4 and err["phi"] < 1e-3 and err["u"] < 2e-2, err
+        assert dD < 1e-6, err
+    else:
+        assert err["rho"] < 2e-2 and err["n"] < 5e-2 and err["phi"] < 5e-2 and err["u"] < 0.5, err
+        assert dD < 2e-5, err
+    sg.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_suspension_64_subset_drift_against_oracle(lbeh, prec):
+    gold = _golden("parity_suspension64.npz")
+    steps, every = int(gold["steps"]), int(gold["every"])
+    w = synth.suspension(n=64, ncoll=3, r=6.0, prec=prec, seed=2)
+    sg = gpu_for(w, lbeh)
+    vs = [np.array(sg.get(("rho",))["cv"])]
+    for _ in range(steps // every):
+        assert sg.step(every) == lbeh.LBEH_OK
+        vs.append(np.array(sg.get(("rho",))["cv"]))
+    v = np.array(vs)
+    vo = gold["v"][: len(v)]
+    vmax = np.abs(vo).max()
+    half = len(v) // 2
+    drift = v[half:, :, 0].mean()
+    drift_o = vo[half:, :, 0].mean()
+    err = {"v_traj": float(np.abs(v - vo).max() / vmax), "drift": float(drift), "drift_oracle": float(drift_o),
+           "drift_rel": float(abs(drift - drift_o) / abs(drift_o))}
+    print("suspension64", prec, steps, err)
+    if prec == "fp32":
+        assert err["v_traj"] < 1e-3 and err["drift_rel"] < 1e-3, err
+    else:
+        assert err["v_traj"] < 5e-2 and err["drift_rel"] < 5e-2, err
+    sg.close()
