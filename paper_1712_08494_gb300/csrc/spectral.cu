@@ -43,6 +43,7 @@ template <typename T> struct AxisDev {
   const unsigned *code;  // butterfly codes of the plan
   const C2<T> *tw;       // twiddles of the plan
   const T *s;            // symbol 2 (1 - cos(2 pi k / n))
+  int code_at, tw_at, s_at;  // offsets of the three tables in the shared-memory table area
 };
 
 template <typename T> struct SArgs {
@@ -51,49 +52,119 @@ template <typename T> struct SArgs {
   AxisDev<T> ax[3];
   Grid3 g;
   T *r, *p, *q, *e, *w;
-  T inv_eref_n;  // 1 / (eps_ref N)
-  int code_cap, tw_cap;  // shared-memory capacity of the plan tables
+  T inv_eref_n;      // 1 / (eps_ref N)
+  int ncode, ntw, ns;  // lengths of the shared-memory tables (all axes)
 };
 
-// Shared memory of a block: the plan of the current pass, its tables, and
-// the two tile buffers.
-template <typename T> struct Smem {
-  LinePlan *P;
-  unsigned *code;
-  C2<T> *tw, *bA, *bB;
+// Per-thread sums of the conjugate-gradient scalars (r.r, r.z, p.q, sum e):
+// a thread adds a few dozen terms in the compute type, and blocks and the grid
+// add the per-thread sums in FP64; the scalars steer the iteration, and the
+// convergence it reports is confirmed by the exact residual.
+template <typename T> struct CgAcc {
+  T v = T(0);
+  __device__ __forceinline__ void add(T x) { v += x; }
+  __device__ __forceinline__ double get() const { return double(v); }
 };
-template <typename T> __device__ Smem<T> smem_layout(unsigned char *raw, const SArgs<T> &a, int pairs_ld) {
+
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// Shared memory of a block, loaded once per launch: the three axes' plans,
+// butterfly codes, twiddles and symbols; then the two tile buffers.
+template <typename T> struct Smem {
+  LinePlan *P;  // [3]
+  unsigned *code;
+  C2<T> *tw;
+  T *sym;
+  C2<T> *bA;  // tile buffers (the second one follows the first)
+};
+template <typename T> __device__ Smem<T> smem_layout(unsigned char *raw, const SArgs<T> &a) {
   Smem<T> m;
   m.P = reinterpret_cast<LinePlan *>(raw);
-  size_t off = (sizeof(LinePlan) + 15) & ~size_t(15);
+  size_t off = (3 * sizeof(LinePlan) + 15) & ~size_t(15);
   m.code = reinterpret_cast<unsigned *>(raw + off);
-  off += ((size_t)a.code_cap * 4 + 15) & ~size_t(15);
+  off += ((size_t)a.ncode * 4 + 15) & ~size_t(15);
   m.tw = reinterpret_cast<C2<T> *>(raw + off);
-  off += ((size_t)a.tw_cap * sizeof(C2<T>) + 15) & ~size_t(15);
+  off += ((size_t)a.ntw * sizeof(C2<T>) + 15) & ~size_t(15);
+  m.sym = reinterpret_cast<T *>(raw + off);
+  off += ((size_t)a.ns * sizeof(T) + 15) & ~size_t(15);
   m.bA = reinterpret_cast<C2<T> *>(raw + off);
-  m.bB = m.bA + pairs_ld;
   return m;
 }
+template <typename T> __device__ void load_tables(const SArgs<T> &a, const Smem<T> &m) {
+  for (int A = 0; A < 3; ++A) {
+    const AxisDev<T> &X = a.ax[A];
+    if (threadIdx.x == 0) m.P[A] = X.P;
+    for (int k = threadIdx.x; k < X.P.ncode; k += blockDim.x) m.code[X.code_at + k] = X.code[k];
+    for (int k = threadIdx.x; k < X.P.ntw; k += blockDim.x) m.tw[X.tw_at + k] = X.tw[k];
+    for (int k = threadIdx.x; k < X.P.n; k += blockDim.x) m.sym[X.s_at + k] = X.s[k];
+  }
+  __syncthreads();
+}
+
+// Staging functors: fetch() issues the global loads of one element (no
+// stores, so a chunk's loads are all in flight together), commit() finishes
+// the element and returns the value to transform.
+template <typename T> struct LoadW {
+  static constexpr int U = kU;
+  const T *w;
+  using V = T;
+  __device__ __forceinline__ V fetch(unsigned i) const { return w[i]; }
+  __device__ __forceinline__ T commit(unsigned, V v) const { return v; }
+};
+// r -= alpha q and e += alpha p (upd), sums of r^2 and e; stages r
+template <typename T> struct LoadU {
+  static constexpr int U = kU / 2;
+  T *r, *e;
+  const T *q, *p;
+  T al;
+  bool upd, he;
+  CgAcc<T> *sr, *se;
+  struct V {
+    T r, q, e, p;
+  };
+  __device__ __forceinline__ V fetch(unsigned i) const {
+    V v;
+    v.r = r[i];
+    v.q = upd ? q[i] : T(0);
+    v.e = upd && he ? e[i] : T(0);
+    v.p = upd ? p[i] : T(0);
+    return v;
+  }
+  __device__ __forceinline__ T commit(unsigned i, const V &v) const {
+    T rv = v.r;
+    if (upd) {
+      rv -= al * v.q;
+      r[i] = rv;
+      const T ev = v.e + al * v.p;
+      e[i] = ev;
+      se->add(ev);
+    }
+    sr->add(rv * rv);
+    return rv;
+  }
+};
+template <typename T> struct StoreW {
+  T *w;
+  __device__ __forceinline__ void operator()(unsigned i, T v) const { w[i] = v; }
+};
 
 // One lattice pass along axis A over every tile owned by this block: stage
-// the tile through `load`, transform each pair of lines (forward; with `fuse`
+// the tile through `ld`, transform each pair of lines (forward; with `fuse`
 // also the symbol scaling and the second transform), write through `store`.
 // Element positions advance without integer division: for the x pass a
 // thread's (line, position) steps by the block size decomposed once; for the
 // y and z passes the tile width W divides the block size, so each thread
 // keeps its line and steps its position.
 template <typename T, class Load, class Store>
-__device__ void tile_pass(const SArgs<T> &a, int A, bool fuse, unsigned char *raw, Load load, Store store) {
+__device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse, const Load &ldr, Store store) {
   const AxisDev<T> &X = a.ax[A];
   const Grid3 g = a.g;
   const int W = X.W, lgW = X.lgW, pairs = W >> 1, ld = X.ld;
-  const Smem<T> sm = smem_layout<T>(raw, a, pairs * ld);
-  // plan of this pass into shared memory
-  if (threadIdx.x == 0) *sm.P = X.P;
-  for (int k = threadIdx.x; k < X.P.ncode; k += blockDim.x) sm.code[k] = X.code[k];
-  for (int k = threadIdx.x; k < X.P.ntw; k += blockDim.x) sm.tw[k] = X.tw[k];
-  __syncthreads();
-  const LinePlan &P = *sm.P;
+  const LinePlan &P = sm.P[A];
+  const unsigned *code = sm.code + X.code_at;
+  const C2<T> *tw = sm.tw + X.tw_at;
+  C2<T> *bA = sm.bA, *bB = sm.bA + pairs * ld;
   const int N = P.n;
   const int nt = tile_count(g, A, W);
   const int xt = (g.nx + W - 1) >> lgW;
@@ -103,26 +174,27 @@ __device__ void tile_pass(const SArgs<T> &a, int A, bool fuse, unsigned char *ra
   // x pass: (line, position) of element tid and the block stride, decomposed once
   const int l0 = threadIdx.x / N, p0 = threadIdx.x - (threadIdx.x / N) * N;
   const int dl = B / N, dp = B - (B / N) * N;
-  const long long nlines = (long long)g.ny * g.nz;
-  const long long sy = g.nx, sz = (long long)g.nx * g.ny;
+  const unsigned nlines = unsigned(g.ny) * unsigned(g.nz);
+  const unsigned sy = unsigned(g.nx), sz = unsigned(g.nx) * unsigned(g.ny);
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
     // tile origin: first row (x pass) or (x0, o) with o = z (y pass) or y (z pass)
     const int o = A == 0 ? 0 : t / xt;
     const int x0 = A == 0 ? 0 : (t - o * xt) << lgW;
-    const long long row0 = (long long)t << lgW;
-    // staging in chunks of kU elements per thread: all loads of a chunk are
-    // issued before the first shared-memory store (latency hiding)
+    const unsigned row0 = unsigned(t) << lgW;
+    // staging in chunks of Load::U elements per thread: all loads of a chunk are
+    // issued before the chunk is finished and stored (latency hiding)
     if (A == 0) {
       int l = l0, pos = p0;
-      for (int el0 = threadIdx.x; el0 < W * N; el0 += kU * B) {
-        T v[kU];
-        int ls[kU], ps[kU];
+      for (int el0 = threadIdx.x; el0 < W * N; el0 += Load::U * B) {
+        typename Load::V v[Load::U];
+        int ls[Load::U], ps[Load::U];
+        bool in[Load::U];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < Load::U; ++u) {
           ls[u] = l;
           ps[u] = pos;
-          const long long row = row0 + l;
-          v[u] = (el0 + u * B < W * N && row < nlines) ? load(row * sy + pos) : T(0);
+          in[u] = el0 + u * B < W * N && row0 + unsigned(l) < nlines;
+          if (in[u]) v[u] = ldr.fetch((row0 + unsigned(l)) * sy + unsigned(pos));
           pos += dp;
           l += dl;
           if (pos >= N) {
@@ -131,38 +203,40 @@ __device__ void tile_pass(const SArgs<T> &a, int A, bool fuse, unsigned char *ra
           }
         }
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
-          if (el0 + u * B < W * N) reinterpret_cast<T *>(sm.bA + (ls[u] >> 1) * ld + ps[u])[ls[u] & 1] = v[u];
+        for (int u = 0; u < Load::U; ++u)
+          if (el0 + u * B < W * N)
+            reinterpret_cast<T *>(bA + (ls[u] >> 1) * ld + ps[u])[ls[u] & 1] =
+                in[u] ? ldr.commit((row0 + unsigned(ls[u])) * sy + unsigned(ps[u]), v[u]) : T(0);
       }
     } else {
       const int l = threadIdx.x & (W - 1);
       const bool ok = x0 + l < g.nx;
-      const long long base = A == 1 ? (long long)o * sz + x0 + l : (long long)o * sy + x0 + l;
-      const long long step = A == 1 ? sy : sz;
+      const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x0 + l);
+      const unsigned step = A == 1 ? sy : sz;
       const int pstep = B >> lgW;
-      T *col = reinterpret_cast<T *>(sm.bA + (l >> 1) * ld) + (l & 1);
-      for (int q0 = threadIdx.x >> lgW; q0 < N; q0 += kU * pstep) {
-        T v[kU];
+      T *col = reinterpret_cast<T *>(bA + (l >> 1) * ld) + (l & 1);
+      for (int q0 = threadIdx.x >> lgW; q0 < N; q0 += Load::U * pstep) {
+        typename Load::V v[Load::U];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < Load::U; ++u) {
           const int pos = q0 + u * pstep;
-          v[u] = (ok && pos < N) ? load(base + pos * step) : T(0);
+          if (ok && pos < N) v[u] = ldr.fetch(base + unsigned(pos) * step);
         }
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
+        for (int u = 0; u < Load::U; ++u) {
           const int pos = q0 + u * pstep;
-          if (pos < N) col[2 * pos] = v[u];
+          if (pos < N) col[2 * pos] = ok ? ldr.commit(base + unsigned(pos) * step, v[u]) : T(0);
         }
       }
     }
     __syncthreads();
-    C2<T> *in = sm.bA, *out = sm.bB;
+    C2<T> *in = bA, *out = bB;
     for (int rep = 0; rep < (fuse ? 2 : 1); ++rep) {
       for (int s = 0; s < P.nst; ++s) {
         const int nb = P.nb[s];
         for (int mi = 0; mi < nm; ++mi) {
           const int m = warp + mi * nw;
-          for (int j = lane; j < nb; j += 32) plan_bfly(P, s, sm.code, sm.tw, in + m * ld, out + m * ld, j);
+          for (int j = lane; j < nb; j += 32) plan_bfly(P, s, code, tw, in + m * ld, out + m * ld, j);
         }
         __syncwarp();
         C2<T> *tp = in;
@@ -170,18 +244,22 @@ __device__ void tile_pass(const SArgs<T> &a, int A, bool fuse, unsigned char *ra
         out = tp;
       }
       if (fuse && rep == 0) {
-        // Hartley values of both lines, times the inverse symbol, packed again
-        const T *sx = a.ax[0].s, *sy_ = a.ax[1].s, *sz_ = a.ax[2].s;
+        // scale -1 / (eps_ref N sum_a s_a(k_a)); the zero mode and missing lines get 0
+        const T *sx = sm.sym + a.ax[0].s_at, *sy_ = sm.sym + a.ax[1].s_at, *sz_ = sm.sym + a.ax[2].s_at;
         for (int mi = 0; mi < nm; ++mi) {
           const int m = warp + mi * nw;
           const int kxa = x0 + 2 * m, kxb = kxa + 1, ky = o;
+          const bool va = kxa < g.nx, vb = kxb < g.nx;
+          const T sxa = va ? sx[kxa] + sy_[ky] : T(1), sxb = vb ? sx[kxb] + sy_[ky] : T(1);
+          const T c = -a.inv_eref_n;
           for (int k = lane; k <= N / 2; k += 32) {
             const Split<T> sp = pair_split(in + m * ld, N, k);
             const int kn = k == 0 ? 0 : N - k;
-            const T sa = kxa < g.nx ? inv_symbol(kxa, ky, k, sx, sy_, sz_, a.inv_eref_n) : T(0);
-            const T sb = kxb < g.nx ? inv_symbol(kxb, ky, k, sx, sy_, sz_, a.inv_eref_n) : T(0);
-            const T sa2 = kxa < g.nx ? inv_symbol(kxa, ky, kn, sx, sy_, sz_, a.inv_eref_n) : T(0);
-            const T sb2 = kxb < g.nx ? inv_symbol(kxb, ky, kn, sx, sy_, sz_, a.inv_eref_n) : T(0);
+            const T szk = sz_[k], szn = sz_[kn];
+            const T sa = va && (kxa | ky | k) ? c * recip(sxa + szk) : T(0);
+            const T sb = vb ? c * recip(sxb + szk) : T(0);
+            const T sa2 = va && (kxa | ky | kn) ? c * recip(sxa + szn) : T(0);
+            const T sb2 = vb ? c * recip(sxb + szn) : T(0);
             out[m * ld + k] = C2<T>{sp.ak * sa, sp.bk * sb};
             out[m * ld + kn] = C2<T>{sp.an * sa2, sp.bn * sb2};
           }
@@ -196,10 +274,9 @@ __device__ void tile_pass(const SArgs<T> &a, int A, bool fuse, unsigned char *ra
     if (A == 0) {
       int l = l0, pos = p0;
       for (int el = threadIdx.x; el < W * N; el += B) {
-        const long long row = row0 + l;
-        if (row < nlines) {
+        if (row0 + unsigned(l) < nlines) {
           const Split<T> sp = pair_split(in + (l >> 1) * ld, N, pos);
-          store(row * sy + pos, (l & 1) ? sp.bk : sp.ak);
+          store((row0 + unsigned(l)) * sy + unsigned(pos), (l & 1) ? sp.bk : sp.ak);
         }
         pos += dp;
         l += dl;
@@ -211,11 +288,11 @@ __device__ void tile_pass(const SArgs<T> &a, int A, bool fuse, unsigned char *ra
     } else {
       const int l = threadIdx.x & (W - 1);
       if (x0 + l < g.nx) {
-        const long long base = A == 1 ? (long long)o * sz + x0 + l : (long long)o * sy + x0 + l;
-        const long long step = A == 1 ? sy : sz;
+        const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x0 + l);
+        const unsigned step = A == 1 ? sy : sz;
         for (int pos = threadIdx.x >> lgW; pos < N; pos += B >> lgW) {
           const Split<T> sp = pair_split(in + (l >> 1) * ld, N, pos);
-          store(base + pos * step, (l & 1) ? sp.bk : sp.ak);
+          store(base + unsigned(pos) * step, (l & 1) ? sp.bk : sp.ak);
         }
       }
     }
@@ -230,8 +307,8 @@ __device__ double matvec_update(const SArgs<T> &a, const T *z, T beta, bool firs
   const Level<T> L0 = a.L0;
   const Dims d = L0.dims();
   const long long G = (long long)gridDim.x * blockDim.x;
-  constexpr int U = 2;  // cells per thread with their loads in flight together
-  SumAcc<DFM> acc;
+  constexpr int U = 4;  // cells per thread with their loads in flight together
+  CgAcc<T> acc;
   Walk wk(blockIdx.x * (long long)blockDim.x + threadIdx.x, G, d.nx, d.ny);
   while (wk.z < d.nz) {
     Nbr c[U];
@@ -273,10 +350,11 @@ __device__ double matvec_update(const SArgs<T> &a, const T *z, T beta, bool firs
 }
 
 template <typename T, bool DFM>
-__global__ void __launch_bounds__(kSB, sizeof(T) == 4 ? 3 : 2) k_spectral(SArgs<T> a) {
+__global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[kSB];
-  unsigned char *buf = smem_raw;
+  const Smem<T> sm = smem_layout<T>(smem_raw, a);
+  load_tables(a, sm);
   const PArgs<T> &pa = a.pa;
   const GridTeam tm{pa.bar, pa.status, pa.spin_limit};
   const Level<T> L0 = a.L0;
@@ -369,24 +447,11 @@ __global__ void __launch_bounds__(kSB, sizeof(T) == 4 ? 3 : 2) k_spectral(SArgs<
     bool first = true;
     for (;;) {
       // U: update r and e, Hartley pass along x of r into w
-      SumAcc<DFM> sr, se;
+      CgAcc<T> sr, se;
       const T al = T(alpha);
       const bool upd = !first, he = have_e;
-      tile_pass<T>(
-          a, 0, false, buf,
-          [&](long long i) {
-            T rv = a.r[i];
-            if (upd) {
-              rv -= al * a.q[i];
-              a.r[i] = rv;
-              const T ev = (he ? a.e[i] : T(0)) + al * a.p[i];
-              a.e[i] = ev;
-              se.add(ev);
-            }
-            sr.add(rv * rv);
-            return rv;
-          },
-          [&](long long i, T v) { a.w[i] = v; });
+      LoadU<T> lu{a.r, a.e, a.q, a.p, al, upd, he, &sr, &se};
+      tile_pass<T>(a, sm, 0, false, lu, StoreW<T>{a.w});
       if (upd) have_e = true;
       {
         const double v0 = block_sum_n(sr.get(), sh);
@@ -406,22 +471,18 @@ __global__ void __launch_bounds__(kSB, sizeof(T) == 4 ? 3 : 2) k_spectral(SArgs<
         if (rr < target || it >= max_iter || !isfinite(rr)) break;
       }
       // preconditioner: Y, Z (scale), Y, X passes on w
-      tile_pass<T>(
-          a, 1, false, buf, [&](long long i) { return a.w[i]; }, [&](long long i, T v) { a.w[i] = v; });
+      const LoadW<T> lw{a.w};
+      tile_pass<T>(a, sm, 1, false, lw, StoreW<T>{a.w});
       if (!tm.sync()) return;
-      tile_pass<T>(
-          a, 2, true, buf, [&](long long i) { return a.w[i]; }, [&](long long i, T v) { a.w[i] = v; });
+      tile_pass<T>(a, sm, 2, true, lw, StoreW<T>{a.w});
       if (!tm.sync()) return;
-      tile_pass<T>(
-          a, 1, false, buf, [&](long long i) { return a.w[i]; }, [&](long long i, T v) { a.w[i] = v; });
+      tile_pass<T>(a, sm, 1, false, lw, StoreW<T>{a.w});
       if (!tm.sync()) return;
-      SumAcc<DFM> srz;
-      tile_pass<T>(
-          a, 0, false, buf, [&](long long i) { return a.w[i]; },
-          [&](long long i, T v) {
-            a.w[i] = v;
-            srz.add(a.r[i] * v);
-          });
+      CgAcc<T> srz;
+      tile_pass<T>(a, sm, 0, false, lw, [&](unsigned i, T v) {
+        a.w[i] = v;
+        srz.add(a.r[i] * v);
+      });
       {
         const double v = block_sum_n(srz.get(), sh);
         if (threadIdx.x == 0) pa.part[blockIdx.x] = v;
@@ -525,7 +586,8 @@ struct Spectral {
   void *sym[3] = {nullptr, nullptr, nullptr};
   LinePlan plan[3];
   int W[3] = {0, 0, 0}, lgW[3] = {0, 0, 0};
-  int code_cap = 0, tw_cap = 0;
+  int code_at[3] = {0, 0, 0}, tw_at[3] = {0, 0, 0}, s_at[3] = {0, 0, 0};
+  int ncode = 0, ntw = 0, ns = 0;
   double eps_ref = 1.0;
 };
 
@@ -556,8 +618,12 @@ template <typename T> static bool spectral_setup(Spectral *s, const Dims &d) {
     if (!build_plan(n, s->plan[A], code, twd)) return false;
     std::vector<C2<T>> tw(twd.size());
     for (size_t k = 0; k < twd.size(); ++k) tw[k] = C2<T>{T(twd[k].x), T(twd[k].y)};
-    s->code_cap = std::max(s->code_cap, (int)code.size());
-    s->tw_cap = std::max(s->tw_cap, (int)tw.size());
+    s->code_at[A] = s->ncode;
+    s->tw_at[A] = s->ntw;
+    s->s_at[A] = s->ns;
+    s->ncode += (int)code.size();
+    s->ntw += (int)tw.size();
+    s->ns += n;
     int W = 32, lg = 5;  // lines per tile: the largest of 32, 16, 8 whose tile fits 40 KB
     while (W > 8 && 2 * (W / 2) * (n + 1) * sizeof(C2<T>) > 40 * 1024) {
       W /= 2;
@@ -576,9 +642,10 @@ template <typename T> static bool spectral_setup(Spectral *s, const Dims &d) {
         cudaMemcpy(s->sym[A], sy.data(), sizeof(T) * n, cudaMemcpyHostToDevice) != cudaSuccess)
       return false;
   }
-  // layout of smem_layout(): plan, codes, twiddles, tile buffers (16-byte aligned parts)
+  // layout of smem_layout(): plans, codes, twiddles, symbols, tile buffers (16-byte aligned parts)
   auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
-  const size_t smem = al(sizeof(LinePlan)) + al((size_t)s->code_cap * 4) + al((size_t)s->tw_cap * sizeof(C2<T>)) + tiles;
+  const size_t smem = al(3 * sizeof(LinePlan)) + al((size_t)s->ncode * 4) + al((size_t)s->ntw * sizeof(C2<T>)) +
+                      al((size_t)s->ns * sizeof(T)) + tiles;
   s->smem = smem;
   constexpr bool DFM = std::is_same<T, float>::value;
   if (!raise_smem_limit((const void *)k_spectral<T, DFM>, smem)) return false;
@@ -634,9 +701,13 @@ template <typename T, bool DFM> static int launch(Spectral *s, const Ctx &c, con
     X.code = (const unsigned *)s->code[A];
     X.tw = (const C2<T> *)s->tw[A];
     X.s = (const T *)s->sym[A];
+    X.code_at = s->code_at[A];
+    X.tw_at = s->tw_at[A];
+    X.s_at = s->s_at[A];
   }
-  a.code_cap = s->code_cap;
-  a.tw_cap = s->tw_cap;
+  a.ncode = s->ncode;
+  a.ntw = s->ntw;
+  a.ns = s->ns;
   a.g = Grid3{c.d.nx, c.d.ny, c.d.nz};
   a.r = (T *)s->r;
   a.p = (T *)s->p;
