@@ -41,10 +41,16 @@ _FIELDS = (2 + 3 + 2 + 1 + 1 + 2) * 4 + (3 + 6) * 4
 COLLIDE_BYTES = {"fp32": 2 * 19 * 4 * 2 + _FIELDS, "bf16": 2 * 19 * 2 * 2 + _FIELDS}
 
 
-# Poisson solve: 16 B/site per fine-level sweep (potential read and written,
-# eps and q read), V(NU_SMOOTH, NU_SMOOTH) cycles
+# Poisson solve, multigrid: 16 B/site per fine-level sweep (potential read
+# and written, eps and q read), V(NU_SMOOTH, NU_SMOOTH) cycles
 POISSON_BYTES_PER_SWEEP = 16
 NU_SMOOTH = 2
+# Poisson solve, spectral conjugate gradients (FP32 words, bytes per site):
+# initial guess and sum of q 36, exact residual 20, final update 20; per
+# iteration 88 = update + x pass 28, y, z, y passes 8 each, x pass with r.z 12,
+# matvec and search direction 24
+SPECTRAL_FIXED_BYTES = 76
+SPECTRAL_ITER_BYTES = 88
 
 
 def collide_bytes(ncomp, pop_bytes, solids):
@@ -188,6 +194,33 @@ def poisson_source_hash():
     return h.hexdigest()[:16]
 
 
+def ncu_spectral_traffic(iters_per_solve):
+    """DRAM bytes per k_spectral launch from the committed ncu summary when it
+    was taken on the current solver source, scaled from the captured launch's
+    iterations to an average solve's by the algorithmic byte rule (else None)."""
+    p = os.path.join(ROOT, "profiles", "k_spectral_droplet128.md")
+    if not os.path.exists(p):
+        return None
+    txt = open(p).read()
+    m = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != spectral_source_hash():
+        return None
+    b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    c = re.search(r"iterations_of_captured_launch:\s*([0-9.eE+]+)", txt)
+    if not b or not c:
+        return None
+    k = float(c.group(1))
+    scale = (SPECTRAL_FIXED_BYTES + SPECTRAL_ITER_BYTES * iters_per_solve) / (SPECTRAL_FIXED_BYTES + SPECTRAL_ITER_BYTES * k)
+    return float(b.group(1)) * scale
+
+
+def spectral_source_hash():
+    h = hashlib.sha256()
+    for f in ("spectral.cu", "spectral.cuh", "poisson_dev.cuh", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1712_08494_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def ncu_poisson_traffic(cycles_per_solve):
     """DRAM bytes per k_poisson launch from the committed ncu summary when it
     was taken on the current solver source: the captured launch's bytes per
@@ -305,6 +338,8 @@ def run_ours(args):
         w = synth.droplet(n=n, r=24.0 * n / 128.0, prec=prec, seed=1 + rank)
         sysg = lbeh.System(w.params, stream.cuda_stream)
         sysg.set_fields(rho=list(w.rho), n=list(w.n))
+        if args.relax:
+            sysg.step(args.relax)  # state preparation: past the start-up transient
         sysg.step(args.warmup)
         torch.cuda.synchronize()
         barrier()
@@ -381,17 +416,44 @@ def run_ours(args):
     t_collb = profb["ms"]["collide"] / max(1, profb["calls"]["collide"]) * 1e-3
     achievedb = COLLIDE_BYTES["bf16"] * N / t_collb / 1e9
     tr = ncu_traffic("fp32")
-    # k_poisson, the kernel with the largest share of the step: one launch is
-    # one solve; algorithmic bytes = 16 B/site per fine-level sweep (potential
-    # read and written, eps, q) times the 2 * NU_SMOOTH fine sweeps of each
-    # V(NU, NU) multigrid cycle
+    # the Poisson kernel: one launch is one solve
     calls_p = max(1, prof["calls"]["poisson"])
     t_pois = prof["ms"]["poisson"] / calls_p * 1e-3
     cyc_solve = prof["poisson_cycles"] / calls_p
-    pois_bytes = POISSON_BYTES_PER_SWEEP * 2 * NU_SMOOTH * cyc_solve * N
+    spectral = results["fp32"]["obs"].poisson_solver == lbeh.LBEH_POISSON_SPECTRAL
+    if spectral:
+        pois_kernel = "k_spectral"
+        pois_bytes = (SPECTRAL_FIXED_BYTES + SPECTRAL_ITER_BYTES * cyc_solve) * N
+        pois_rule = "%d + %d k B/site, k = conjugate-gradient iterations of the solve" % (
+            SPECTRAL_FIXED_BYTES, SPECTRAL_ITER_BYTES)
+        tr_p = ncu_spectral_traffic(cyc_solve)
+    else:
+        pois_kernel = "k_poisson"
+        pois_bytes = POISSON_BYTES_PER_SWEEP * 2 * NU_SMOOTH * cyc_solve * N
+        pois_rule = "16 B/site x 2*%d fine sweeps per V(%d,%d) cycle" % (NU_SMOOTH, NU_SMOOTH, NU_SMOOTH)
+        tr_p = ncu_poisson_traffic(cyc_solve)
     achieved_p = pois_bytes / t_pois / 1e9 if t_pois > 0 else 0.0
-    tr_p = ncu_poisson_traffic(cyc_solve)
 
+    # whole-step roofline by the survey's rule: 340 + 16 s B/site (FP32, two
+    # components), s = Poisson fine-sweep equivalents of 16 B/site
+    s_eq = pois_bytes / N / POISSON_BYTES_PER_SWEEP * (prof["calls"]["poisson"] / max(1, prof["calls"]["collide"]))
+    step_bytes = 340 + POISSON_BYTES_PER_SWEEP * s_eq
+    step_gbs = step_bytes * N * args.steps / (ms32 * 1e-3) / 1e9
+    step_roof = {"bytes_per_site": step_bytes, "achieved_gbs": step_gbs, "peak": peak, "frac": step_gbs / peak,
+                 "rule": "340 + 16 s B/site, s = Poisson bytes per site / 16"}
+    roof_p = {"bound": "hbm", "kernel": pois_kernel, "achieved": achieved_p, "peak": peak, "peak_kind": peak_kind,
+              "unit": "GB/s", "frac": achieved_p / peak, "traffic": tr_p, "algorithmic_bytes_per_launch": pois_bytes,
+              "avg_launch_ms": t_pois * 1e3, "iterations_per_launch": cyc_solve, "bytes_rule": pois_rule}
+    roof_c = {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak, "peak_kind": peak_kind,
+              "unit": "GB/s", "frac": achieved / peak, "traffic": tr,
+              "algorithmic_bytes_per_launch": COLLIDE_BYTES["fp32"] * N, "avg_launch_ms": t_coll * 1e3,
+              "bytes_rule": "%d B/site: populations read and written, fields read once, u and face fluxes written"
+                            % COLLIDE_BYTES["fp32"]}
+    # `roofline` is the kernel with the larger share of the step
+    if prof["ms"]["poisson"] >= prof["ms"]["collide"]:
+        roof_main, roof_other_key, roof_other = roof_p, "roofline_collide", roof_c
+    else:
+        roof_main, roof_other_key, roof_other = roof_c, "roofline_poisson", roof_p
     if rank != 0:
         return
     extra = {}
@@ -408,6 +470,9 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "dielectric droplet %d^3, 2 components + 2 ion species, E_z=1e-3" % n,
                    "sites": N, "populations": "fp32", "poisson_tol": 1e-6,
+                   "poisson_solver": "spectral" if spectral else "multigrid",
+                   "state": ("relaxed for %d steps before the warm-up (the workload runs 5000 steps; the first "
+                             "steps are its start-up transient)" % args.relax) if args.relax else "initial",
                    "l2": "inputs larger than L2 (populations %.0f MB)" % (2 * 19 * 4 * N / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
         "bf16_storage": {"value": mlupsbf, "unit": "MLUPS", "speedup_vs_fp32": mlupsbf / mlups32,
@@ -416,17 +481,11 @@ def run_ours(args):
                          "deformation_bf16": results["bf16"]["obs"].deformation,
                          "ms_per_step": msbf / args.steps,
                          "collide_gbs": achievedb},
-        "roofline": {"bound": "hbm", "kernel": "k_poisson", "achieved": achieved_p, "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved_p / peak, "traffic": tr_p,
-                     "algorithmic_bytes_per_launch": pois_bytes, "avg_launch_ms": t_pois * 1e3,
-                     "multigrid_cycles_per_launch": cyc_solve,
-                     "bytes_rule": "16 B/site x 2*%d fine sweeps per V(%d,%d) cycle" % (NU_SMOOTH, NU_SMOOTH, NU_SMOOTH)},
-        "roofline_collide": {"bound": "hbm", "kernel": "k_collide", "achieved": achieved, "peak": peak,
-                             "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": tr,
-                             "algorithmic_bytes_per_launch": COLLIDE_BYTES["fp32"] * N,
-                             "avg_launch_ms": t_coll * 1e3},
+        "roofline": roof_main,
+        roof_other_key: roof_other,
         "stage_share": {k: (v / total_ms if total_ms else None) for k, v in prof["ms"].items()},
-        "poisson_cycles_per_step": results["fp32"]["cycles"] / args.steps,
+        "step_roofline": step_roof,
+        "poisson_iterations_per_step": results["fp32"]["cycles"] / args.steps,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": prof["launches"],
     }
     line.update(extra)
@@ -470,8 +529,17 @@ def suspension_run(lbeh, stream, peak, peak_kind, args, n=256, steps=100):
         t_coll = prof["ms"]["collide"] / max(1, prof["calls"]["collide"]) * 1e-3
         gbs = collide_bytes(1, 4 if prec == "fp32" else 2, True) * n ** 3 / t_coll / 1e9
         total = sum(prof["ms"].values())
+        # whole-step roofline by the survey's rule: 172 + 16 s B/site (FP32) or
+        # 96 + 16 s (BF16) for one component, s = Poisson fine-sweep equivalents
+        sweeps = 2 * NU_SMOOTH * cycles / steps
+        step_bytes = (172 if prec == "fp32" else 96) + POISSON_BYTES_PER_SWEEP * sweeps
+        step_gbs = step_bytes * n ** 3 * steps / (ms * 1e-3) / 1e9
         out[prec] = {"mlups": n ** 3 * steps / (ms * 1e3), "ms_per_step": ms / steps, "status": rc,
                      "poisson_cycles_per_step": cycles / steps,
+                     "step_roofline": {"bytes_per_site": step_bytes, "achieved_gbs": step_gbs, "peak": peak,
+                                       "frac": step_gbs / peak,
+                                       "rule": "%d + 16 s B/site, s = 4 fine sweeps x multigrid cycles per step"
+                                               % (172 if prec == "fp32" else 96)},
                      "collide_gbs": gbs, "collide_frac": gbs / peak, "peak_kind": peak_kind,
                      "stage_share": {k: (v / total if total else None) for k, v in prof["ms"].items()}}
     out["bf16_speedup"] = out["bf16"]["mlups"] / out["fp32"]["mlups"]
@@ -534,6 +602,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--size", type=int, default=SIZE)
+    ap.add_argument("--relax", type=int, default=200,
+                    help="untimed steps before the warm-up that take the droplet past its start-up transient")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the suspension, batch and adjoint measurements")
