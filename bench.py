@@ -334,7 +334,7 @@ def run_ours(args):
     results = {}
     fields = {}
     sampler = None
-    for prec in ("fp32", "bf16"):
+    for prec in ("fp32", "bf16", "fp16"):
         w = synth.droplet(n=n, r=24.0 * n / 128.0, prec=prec, seed=1 + rank)
         sysg = lbeh.System(w.params, stream.cuda_stream)
         sysg.set_fields(rho=list(w.rho), n=list(w.n))
@@ -459,11 +459,27 @@ def run_ours(args):
     extra = {}
     if not args.no_extra:
         extra["suspension"] = suspension_run(lbeh, stream, peak, peak_kind, args)
+        extra["showcase"] = showcase_run(lbeh, stream, args)
         extra["batch"] = batch_run(lbeh, stream, args)
         extra["adjoint"] = adjoint_run(lbeh, stream, args)
     cpu = None if args.no_cpu_baseline else cpu_baseline(n)
     clocks = sampler.summary() if sampler else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
     total_ms = sum(prof["ms"].values())
+
+    def half_storage(prec):
+        """Rate and deviation from the FP32 run of a reduced-precision storage mode."""
+        r = results[prec]
+        mlups = world * N * args.steps / (r["ms"] * 1e3)
+        dev = max(float(np.abs(fields[prec][s] - fields["fp32"][s]).max() / np.abs(fields["fp32"][s]).max())
+                  for s in range(2))
+        rms = max(float(np.sqrt(((fields[prec][s] - fields["fp32"][s]) ** 2).mean() / (fields["fp32"][s] ** 2).mean()))
+                  for s in range(2))
+        pr = r["prof"]
+        return {"value": mlups, "unit": "MLUPS", "speedup_vs_fp32": mlups / mlups32, "max_rel_dev_rho_vs_fp32": dev,
+                "rms_rel_dev_rho_vs_fp32": rms, "deformation": r["obs"].deformation,
+                "ms_per_step": r["ms"] / args.steps, "poisson_iterations_per_step": r["cycles"] / args.steps,
+                "stage_ms_per_step": {k: v / max(1, pr["calls"]["collide"]) for k, v in pr["ms"].items()}}
+
     line = {
         "metric": METRIC, "value": mlups32, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32 / args.steps, "higher_is_better": True,
@@ -475,15 +491,19 @@ def run_ours(args):
                              "steps are its start-up transient)" % args.relax) if args.relax else "initial",
                    "l2": "inputs larger than L2 (populations %.0f MB)" % (2 * 19 * 4 * N / 1e6),
                    "parallelism": "replicas" if world > 1 else "single"},
+        "fp16_storage": half_storage("fp16"),
         "bf16_storage": {"value": mlupsbf, "unit": "MLUPS", "speedup_vs_fp32": mlupsbf / mlups32,
                          "max_rel_dev_rho_vs_fp32": err_bf, "rms_rel_dev_rho_vs_fp32": rms_bf,
                          "deformation_fp32": results["fp32"]["obs"].deformation,
                          "deformation_bf16": results["bf16"]["obs"].deformation,
                          "ms_per_step": msbf / args.steps,
-                         "collide_gbs": achievedb},
+                         "collide_gbs": achievedb,
+                         "poisson_iterations_per_step": results["bf16"]["cycles"] / args.steps,
+                         "stage_ms_per_step": {k: v / max(1, profb["calls"]["collide"]) for k, v in profb["ms"].items()}},
         "roofline": roof_main,
         roof_other_key: roof_other,
         "stage_share": {k: (v / total_ms if total_ms else None) for k, v in prof["ms"].items()},
+        "stage_ms_per_step": {k: v / max(1, prof["calls"]["collide"]) for k, v in prof["ms"].items()},
         "step_roofline": step_roof,
         "poisson_iterations_per_step": results["fp32"]["cycles"] / args.steps,
         "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": prof["launches"],
@@ -545,6 +565,31 @@ def suspension_run(lbeh, stream, peak, peak_kind, args, n=256, steps=100):
     out["bf16_speedup"] = out["bf16"]["mlups"] / out["fp32"]["mlups"]
     out["bf16_colloid_vx_rel_dev"] = float(np.abs(vx["bf16"] - vx["fp32"]).max() / max(np.abs(vx["fp32"]).max(), 1e-30))
     return out
+
+
+def showcase_run(lbeh, stream, args, n=384, r=64.0, steps=20):
+    """The paper's largest run (Sec. III.D, 3D charged droplet): a drop of
+    radius 64 in a 384^3 periodic box, two components (G = 4), salt 1e-3,
+    Gibbs transfer energies +-4 kT (the drop takes a negative net charge),
+    equal permittivities, applied field 1e-3 along z; FP32.  Device memory of
+    the system and MLUPS over `steps` steps after 5 warm-up steps."""
+    import torch
+    import synth
+    free0, total = torch.cuda.mem_get_info()
+    w = synth.droplet(n=n, r=r, prec="fp32", salt=1e-3, Ez=1e-3, eps_r=(1.0, 1.0), noise=0.01)
+    w.params.dmu = (4.0, -4.0)
+    s = lbeh.System(w.params, stream.cuda_stream)
+    s.set_fields(rho=list(w.rho), n=list(w.n))
+    del w
+    free1, _ = torch.cuda.mem_get_info()
+    s.step(5)
+    ms, rc = _timed(s.step, stream, steps)
+    o = s.observables()
+    s.close()
+    return {"workload": "charged droplet %d^3, r=%g, salt 1e-3, dmu +-4, E_z=1e-3, FP32" % (n, r), "sites": n ** 3,
+            "steps": steps, "mlups": n ** 3 * steps / (ms * 1e3), "ms_per_step": ms / steps, "status": rc,
+            "device_gb": (free0 - free1) / 1e9, "poisson_solver": "spectral" if o.poisson_solver == 2 else "multigrid",
+            "poisson_iterations_last_step": o.poisson_iters}
 
 
 def batch_run(lbeh, stream, args, steps=50):

@@ -18,6 +18,7 @@
 //   F  p = z + beta p, q = A z + beta q (sum p.q).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -71,12 +72,21 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 
 // Shared memory of a block, loaded once per launch: the three axes' plans,
 // butterfly codes, twiddles and symbols; then the two tile buffers.
+// Lines of N = 32 K points (K = 1, 2, 4, 8) are transformed in registers by
+// one warp (warp_fft below); its per-lane twiddles live in shared memory:
+// kLaneTw slots per lane and axis, K - 1 of W_N^(lane kappa) then the five
+// cross-lane stage twiddles.
+constexpr int kLaneTw = 12;
+__host__ __device__ inline int reg_fft_k(int N) {
+  return (N == 32 || N == 64 || N == 128 || N == 256) ? N / 32 : 0;
+}
 template <typename T> struct Smem {
   LinePlan *P;  // [3]
   unsigned *code;
   C2<T> *tw;
   T *sym;
-  C2<T> *bA;  // tile buffers (the second one follows the first)
+  C2<T> *lanetw;  // [3][32][kLaneTw]
+  C2<T> *bA;      // tile buffers (the second one follows the first)
 };
 template <typename T> __device__ Smem<T> smem_layout(unsigned char *raw, const SArgs<T> &a) {
   Smem<T> m;
@@ -88,8 +98,19 @@ template <typename T> __device__ Smem<T> smem_layout(unsigned char *raw, const S
   off += ((size_t)a.ntw * sizeof(C2<T>) + 15) & ~size_t(15);
   m.sym = reinterpret_cast<T *>(raw + off);
   off += ((size_t)a.ns * sizeof(T) + 15) & ~size_t(15);
+  m.lanetw = reinterpret_cast<C2<T> *>(raw + off);
+  off += (size_t)3 * 32 * kLaneTw * sizeof(C2<T>);
   m.bA = reinterpret_cast<C2<T> *>(raw + off);
   return m;
+}
+
+__device__ __forceinline__ void sincos_pi(float x, float *s, float *c) { sincospif(x, s, c); }
+__device__ __forceinline__ void sincos_pi(double x, double *s, double *c) { sincospi(x, s, c); }
+// exp(-2 pi i t / n)
+template <typename T> __device__ __forceinline__ C2<T> root(int t, int n) {
+  T sn, cs;
+  sincos_pi(T(2) * T(t) / T(n), &sn, &cs);
+  return C2<T>{cs, -sn};
 }
 template <typename T> __device__ void load_tables(const SArgs<T> &a, const Smem<T> &m) {
   for (int A = 0; A < 3; ++A) {
@@ -98,8 +119,56 @@ template <typename T> __device__ void load_tables(const SArgs<T> &a, const Smem<
     for (int k = threadIdx.x; k < X.P.ncode; k += blockDim.x) m.code[X.code_at + k] = X.code[k];
     for (int k = threadIdx.x; k < X.P.ntw; k += blockDim.x) m.tw[X.tw_at + k] = X.tw[k];
     for (int k = threadIdx.x; k < X.P.n; k += blockDim.x) m.sym[X.s_at + k] = X.s[k];
+    const int K = reg_fft_k(X.P.n);
+    if (K && threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      C2<T> *lt = m.lanetw + (A * 32 + lane) * kLaneTw;
+      for (int kap = 1; kap < K; ++kap) lt[kap - 1] = root<T>(lane * kap, X.P.n);
+      for (int st = 0; st < 5; ++st) {
+        const int h = 16 >> st;
+        lt[7 + st] = root<T>((lane & (h - 1)) * (16 / h), 32);
+      }
+    }
   }
   __syncthreads();
+}
+
+// In-place transform of one complex line X[0, 32 K) by a warp: lane l takes
+// x[l + 32 k] (k < K), does the K-point DFTs in registers, multiplies by
+// W_N^(l kappa), then the 32-point DFTs across the lanes by five radix-2
+// decimation-in-frequency stages with shuffles (the result of lane l is
+// X[kappa + K bitrev5(l)]) and writes the line back in natural order.
+template <typename T, int K>
+__device__ __forceinline__ void warp_fft(C2<T> *X, const C2<T> *lt, int lane) {
+  C2<T> v[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = X[lane + 32 * k];
+  if constexpr (K > 1) Dft<T, K>::run(v, nullptr, 0);
+#pragma unroll
+  for (int kap = 1; kap < K; ++kap) v[kap] = cmul(v[kap], lt[kap - 1]);
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int h = 16 >> st;
+    const bool bottom = (lane & h) != 0;
+    const C2<T> w = lt[7 + st];
+#pragma unroll
+    for (int kap = 0; kap < K; ++kap) {
+      C2<T> u;
+      u.x = __shfl_xor_sync(0xffffffffu, v[kap].x, h);
+      u.y = __shfl_xor_sync(0xffffffffu, v[kap].y, h);
+      v[kap] = bottom ? cmul(csub(u, v[kap]), w) : cadd(v[kap], u);
+    }
+  }
+  const int br = int(__brev(unsigned(lane)) >> 27);
+  __syncwarp();
+#pragma unroll
+  for (int kap = 0; kap < K; ++kap) X[kap + K * br] = v[kap];
+  __syncwarp();
+}
+template <typename T, int K>
+__device__ __forceinline__ void warp_fft_lines(C2<T> *buf, int nm, int warp, int nw, int ld, const C2<T> *lt,
+                                               int lane) {
+  for (int mi = 0; mi < nm; ++mi) warp_fft<T, K>(buf + (warp + mi * nw) * ld, lt, lane);
 }
 
 // Staging functors: fetch() issues the global loads of one element (no
@@ -166,6 +235,7 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse
   const C2<T> *tw = sm.tw + X.tw_at;
   C2<T> *bA = sm.bA, *bB = sm.bA + pairs * ld;
   const int N = P.n;
+  const int regK = reg_fft_k(N);  // register transform of the lines, or the plan's stages
   const int nt = tile_count(g, A, W);
   const int xt = (g.nx + W - 1) >> lgW;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -232,16 +302,26 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse
     __syncthreads();
     C2<T> *in = bA, *out = bB;
     for (int rep = 0; rep < (fuse ? 2 : 1); ++rep) {
-      for (int s = 0; s < P.nst; ++s) {
-        const int nb = P.nb[s];
-        for (int mi = 0; mi < nm; ++mi) {
-          const int m = warp + mi * nw;
-          for (int j = lane; j < nb; j += 32) plan_bfly(P, s, code, tw, in + m * ld, out + m * ld, j);
+      if (regK) {
+        const C2<T> *lt = sm.lanetw + (A * 32 + lane) * kLaneTw;
+        switch (regK) {
+          case 1: warp_fft_lines<T, 1>(in, nm, warp, nw, ld, lt, lane); break;
+          case 2: warp_fft_lines<T, 2>(in, nm, warp, nw, ld, lt, lane); break;
+          case 4: warp_fft_lines<T, 4>(in, nm, warp, nw, ld, lt, lane); break;
+          default: warp_fft_lines<T, 8>(in, nm, warp, nw, ld, lt, lane); break;
         }
-        __syncwarp();
-        C2<T> *tp = in;
-        in = out;
-        out = tp;
+      } else {
+        for (int s = 0; s < P.nst; ++s) {
+          const int nb = P.nb[s];
+          for (int mi = 0; mi < nm; ++mi) {
+            const int m = warp + mi * nw;
+            for (int j = lane; j < nb; j += 32) plan_bfly(P, s, code, tw, in + m * ld, out + m * ld, j);
+          }
+          __syncwarp();
+          C2<T> *tp = in;
+          in = out;
+          out = tp;
+        }
       }
       if (fuse && rep == 0) {
         // scale -1 / (eps_ref N sum_a s_a(k_a)); the zero mode and missing lines get 0
@@ -349,6 +429,91 @@ __device__ double matvec_update(const SArgs<T> &a, const T *z, T beta, bool firs
   return block_sum_n(acc.get(), sh);
 }
 
+// Exact residual r = b - A phi with b = -(q - qbar) + sum_d k (E_ext . c_d)
+// (FP64, or double-float words in the FP32 modes: the arithmetic of
+// residual_site in poisson_dev.cuh), two cells per thread with all their
+// loads in flight together; block partials of |r|^2, |b|^2 and sum phi.
+template <typename T, bool DFM>
+__device__ void residual_cells(const SArgs<T> &a, double qbar, DF qbar_df, double *sh, double &ar, double &ab,
+                               double &ap) {
+  const PArgs<T> &pa = a.pa;
+  const Level<T> &L0 = a.L0;
+  const Dims d = L0.dims();
+  const long long G = (long long)gridDim.x * blockDim.x;
+  constexpr int U = 2;
+  SumAcc<DFM> sr, sb, sp;
+  Walk wk(blockIdx.x * (long long)blockDim.x + threadIdx.x, G, d.nx, d.ny);
+  while (wk.z < d.nz) {
+    Nbr c[U];
+    bool v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v[u] = wk.z < d.nz;
+      c[u] = nbr(d, v[u] ? wk.u : 0, v[u] ? wk.y : 0, v[u] ? wk.z : 0);
+      if (v[u]) wk.next();
+    }
+    using P = typename std::conditional<DFM, float, double>::type;
+    P ph[U][7], pl[U][7];
+    T ev[U][7], qv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const unsigned idx[7] = {c[u].i, c[u].xp, c[u].xm, c[u].yp, c[u].ym, c[u].zp, c[u].zm};
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        if constexpr (DFM) {
+          ph[u][k] = pa.phi_hi[idx[k]];
+          pl[u][k] = pa.phi_lo[idx[k]];
+        } else {
+          ph[u][k] = pa.phi[idx[k]];
+          pl[u][k] = 0.0;
+        }
+        ev[u][k] = L0.eps[idx[k]];
+      }
+      qv[u] = pa.q[c[u].i];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (!v[u]) continue;
+      T kf[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) kf[k] = T(0.5) * (ev[u][0] + ev[u][k + 1]);
+      if constexpr (DFM) {
+        const DF p{ph[u][0], pl[u][0]};
+        DF Ap = df_mul_f(df_sub(DF{ph[u][1], pl[u][1]}, p), kf[0]);
+#pragma unroll
+        for (int k = 1; k < 6; ++k) Ap = df_add(Ap, df_mul_f(df_sub(DF{ph[u][k + 1], pl[u][k + 1]}, p), kf[k]));
+        DF b = df_sub(qbar_df, DF{float(qv[u]), 0.f});
+        if (pa.edf[0].hi != 0.f) b = df_add(b, df_mul(pa.edf[0], two_sum(kf[0], -kf[1])));
+        if (pa.edf[1].hi != 0.f) b = df_add(b, df_mul(pa.edf[1], two_sum(kf[2], -kf[3])));
+        if (pa.edf[2].hi != 0.f) b = df_add(b, df_mul(pa.edf[2], two_sum(kf[4], -kf[5])));
+        const DF r = df_sub(b, Ap);
+        const float rf = __fadd_rn(r.hi, r.lo);
+        L0.b[c[u].i] = T(rf);
+        sr.add(rf * rf);
+        sb.add(b.hi * b.hi);
+        sp.add(p.hi);
+      } else {
+        const double p = ph[u][0];
+        double b = -(double(qv[u]) - qbar);
+        if (pa.ex != 0.0) b += pa.ex * (double(kf[0]) - double(kf[1]));
+        if (pa.ey != 0.0) b += pa.ey * (double(kf[2]) - double(kf[3]));
+        if (pa.ez != 0.0) b += pa.ez * (double(kf[4]) - double(kf[5]));
+        const double Ap = double(kf[0]) * (ph[u][1] - p) - double(kf[1]) * (p - ph[u][2]) +
+                          double(kf[2]) * (ph[u][3] - p) - double(kf[3]) * (p - ph[u][4]) +
+                          double(kf[4]) * (ph[u][5] - p) - double(kf[5]) * (p - ph[u][6]);
+        const double r = b - Ap;
+        L0.b[c[u].i] = T(r);
+        sr.add(r * r);
+        sb.add(b * b);
+        sp.add(p);
+      }
+    }
+  }
+  ar = block_sum_n(sr.get(), sh);
+  ab = block_sum_n(sb.get(), sh);
+  ap = block_sum_n(sp.get(), sh);
+}
+
 template <typename T, bool DFM>
 __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -430,8 +595,19 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   for (int outer = 0;; ++outer) {
     // exact residual r = b - A phi (FP64 / double-float), |r|^2, |b|^2, sum phi
     double r2, b2, ps;
-    // (L2 prefetch hints: the potential and eps come from DRAM after the step's other kernels)
-    if (!residual_pass<T, DFM>(pa, tm, L0, qbar, qbar_df, sh, r2, b2, ps, true)) return;
+    {
+      double ar, ab, ap;
+      residual_cells<T, DFM>(a, qbar, qbar_df, sh, ar, ab, ap);
+      if (threadIdx.x == 0) {
+        pa.part[blockIdx.x] = ar;
+        pa.part[nb + blockIdx.x] = ab;
+        pa.part[2 * nb + blockIdx.x] = ap;
+      }
+      if (!tm.sync()) return;
+      r2 = sum_partials(pa.part, nb, sh);
+      b2 = sum_partials(pa.part + nb, nb, sh);
+      ps = sum_partials(pa.part + 2 * nb, nb, sh);
+    }
     if (outer == 0) bn = b2;
     rr = rel_res(r2, bn);
     exact = true;
@@ -645,7 +821,7 @@ template <typename T> static bool spectral_setup(Spectral *s, const Dims &d) {
   // layout of smem_layout(): plans, codes, twiddles, symbols, tile buffers (16-byte aligned parts)
   auto al = [](size_t b) { return (b + 15) & ~size_t(15); };
   const size_t smem = al(3 * sizeof(LinePlan)) + al((size_t)s->ncode * 4) + al((size_t)s->ntw * sizeof(C2<T>)) +
-                      al((size_t)s->ns * sizeof(T)) + tiles;
+                      al((size_t)s->ns * sizeof(T)) + (size_t)3 * 32 * kLaneTw * sizeof(C2<T>) + tiles;
   s->smem = smem;
   constexpr bool DFM = std::is_same<T, float>::value;
   if (!raise_smem_limit((const void *)k_spectral<T, DFM>, smem)) return false;

@@ -245,6 +245,40 @@ def flat_interface(nx=512, ny=4, nz=4, dmu=(2.0, -2.0), chi=0.0, salt=1e-3, G=4.
                     note="flat interfaces, dmu=%s, chi=%g" % (tuple(dmu), chi))
 
 
+def interface_colloid(n=64, r=8.0, dz=0.0, salt=0.0, dmu=(4.0, 4.0), q=0.0, G=4.0, prec="fp32",
+                      rho_major=0.7, rho_minor=0.04, tol=1e-6) -> Workload:
+    """A sphere at a flat fluid interface (Sec. III.F): fluid a (red) for
+    z < n/2, fluid b above (interfaces at z = n/2 - 1/2 and at the periodic
+    boundary), one moving sphere of radius r centred dz above the middle
+    interface with charge q, colloid permittivity 10/80 of the fluids'.  With
+    salt > 0 the ions start at the bulk Boltzmann ratio of their Gibbs transfer
+    energies, salt in fluid a and salt exp(-dmu) in fluid b; counter-ions
+    for q are spread over nodes more than r + 2 from the sphere."""
+    shape = (n, n, n)
+    x, y, z = _grid(n, n, n)
+    in_a = z < n // 2
+    red = np.where(in_a, rho_major, rho_minor)
+    blue = np.where(in_a, rho_minor, rho_major)
+    rho = np.stack([red, blue])
+    cx = np.array([[n / 2.0 + 0.25, n / 2.0 - 0.25, n / 2.0 - 0.5 + dz]])
+    cr = np.array([float(r)])
+    cq = np.array([float(q)])
+    nions = 2 if (salt > 0.0 or q != 0.0) else 0
+    ions = None
+    if nions:
+        ions = np.stack([np.where(in_a, salt, salt * math.exp(-dmu[0])),
+                         np.where(in_a, salt, salt * math.exp(-dmu[1]))]).astype(np.float64)
+        if q != 0.0:
+            far = _far_mask(n, n, n, cx, cr, 2.0)
+            ions[0 if q < 0 else 1][far] += abs(q) / far.sum()
+    p = Params(nx=n, ny=n, nz=n, ncomp=2, nions=nions, prec=prec, tau=1.0, G=G, D=0.05, bjerrum=0.4,
+               eps_r=(1.0, 1.0), eps_r_colloid=0.125, dmu=tuple(float(v) for v in dmu) if nions else (0.0, 0.0),
+               drho_a=rho_major - rho_minor, E_ext=(0.0, 0.0, 0.0), poisson_tol=tol, poisson_max_iter=200,
+               ncolloid_max=1, colloids_move=1, rho0_shift=(rho_minor, rho_minor))
+    return Workload("interface_colloid_%d" % n, p, rho, ions, cx, np.zeros_like(cx), cq, cr, steps=1,
+                    note="sphere r=%g at a flat interface, dz=%g, salt=%g" % (r, dz, salt))
+
+
 def shear_wave(n=32, U=1e-3, rho=1.0, tau=1.0) -> Workload:
     """Single-component, ion-free periodic box whose initial velocity is the
     shear wave u_x(z) = U sin(2 pi z / n) (density uniform)."""

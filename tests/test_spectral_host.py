@@ -134,3 +134,36 @@ def test_device_solver_compiles_for_sm103a(tmp_path):
     subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-std=c++17", "--expt-relaxed-constexpr",
                     "-I", CSRC, "-c", os.path.join(CSRC, "spectral.cu"), "-o", str(tmp_path / "spectral.o")],
                    check=True, capture_output=True)
+
+
+def _warp_fft_lanes(x, K):
+    """The register line transform of the device solver written out over the
+    32 lanes of a warp: lane l takes x[l + 32 k], K-point DFTs, twiddles
+    W_N^(l kappa), five radix-2 decimation-in-frequency stages across lanes
+    (partner l ^ h, bottom lanes (u - v) W_2h^(l mod h)), result of lane l at
+    kappa + K bitrev5(l)."""
+    N = 32 * K
+    lane = np.arange(32)
+    v = np.stack([x[lane + 32 * k] for k in range(K)], axis=1).astype(complex)
+    W = np.exp(-2j * np.pi * np.outer(np.arange(K), np.arange(K)) / K)
+    v = v @ W.T
+    for kap in range(1, K):
+        v[:, kap] *= np.exp(-2j * np.pi * lane * kap / N)
+    for st in range(5):
+        h = 16 >> st
+        u = v[lane ^ h]
+        bottom = (lane & h) != 0
+        w = np.exp(-2j * np.pi * ((lane & (h - 1)) * (16 // h)) / 32)
+        v = np.where(bottom[:, None], (u - v) * w[:, None], v + u)
+    br = np.array([int("{:05b}".format(l)[::-1], 2) for l in lane])
+    out = np.zeros(N, complex)
+    for kap in range(K):
+        out[kap + K * br] = v[:, kap]
+    return out
+
+
+@pytest.mark.parametrize("K", [1, 2, 4, 8])
+def test_register_line_transform_lane_algorithm(K):
+    rng = np.random.default_rng(K)
+    x = rng.normal(size=32 * K) + 1j * rng.normal(size=32 * K)
+    assert np.abs(_warp_fft_lanes(x, K) - np.fft.fft(x)).max() < 1e-12 * np.abs(x).sum()
