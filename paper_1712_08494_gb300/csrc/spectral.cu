@@ -174,12 +174,28 @@ __device__ __forceinline__ void warp_fft_lines(C2<T> *buf, int nm, int warp, int
 // Staging functors: fetch() issues the global loads of one element (no
 // stores, so a chunk's loads are all in flight together), commit() finishes
 // the element and returns the value to transform.
+// The aux slot is the element's place in the second tile buffer when the
+// lines are transformed in place (register transform), else null: a pass can
+// keep a second value per element there for its store.
 template <typename T> struct LoadW {
   static constexpr int U = kU;
   const T *w;
   using V = T;
   __device__ __forceinline__ V fetch(unsigned i) const { return w[i]; }
-  __device__ __forceinline__ T commit(unsigned, V v) const { return v; }
+  __device__ __forceinline__ T commit(unsigned, V v, T *) const { return v; }
+};
+// stages w and keeps r in the aux slot (the last x pass: r.z at the store)
+template <typename T> struct LoadWR {
+  static constexpr int U = kU / 2;
+  const T *w, *r;
+  struct V {
+    T w, r;
+  };
+  __device__ __forceinline__ V fetch(unsigned i) const { return V{w[i], r[i]}; }
+  __device__ __forceinline__ T commit(unsigned, const V &v, T *aux) const {
+    if (aux) *aux = v.r;
+    return v.w;
+  }
 };
 // r -= alpha q and e += alpha p (upd), sums of r^2 and e; stages r
 template <typename T> struct LoadU {
@@ -200,7 +216,7 @@ template <typename T> struct LoadU {
     v.p = upd ? p[i] : T(0);
     return v;
   }
-  __device__ __forceinline__ T commit(unsigned i, const V &v) const {
+  __device__ __forceinline__ T commit(unsigned i, const V &v, T *) const {
     T rv = v.r;
     if (upd) {
       rv -= al * v.q;
@@ -215,7 +231,17 @@ template <typename T> struct LoadU {
 };
 template <typename T> struct StoreW {
   T *w;
-  __device__ __forceinline__ void operator()(unsigned i, T v) const { w[i] = v; }
+  __device__ __forceinline__ void operator()(unsigned i, T v, const T *) const { w[i] = v; }
+};
+// stores z and adds r.z (r from the aux slot, else from memory)
+template <typename T> struct StoreRZ {
+  T *w;
+  const T *r;
+  CgAcc<T> *acc;
+  __device__ __forceinline__ void operator()(unsigned i, T v, const T *aux) const {
+    w[i] = v;
+    acc->add((aux ? *aux : r[i]) * v);
+  }
 };
 
 // One lattice pass along axis A over every tile owned by this block: stage
@@ -274,9 +300,12 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse
         }
 #pragma unroll
         for (int u = 0; u < Load::U; ++u)
-          if (el0 + u * B < W * N)
-            reinterpret_cast<T *>(bA + (ls[u] >> 1) * ld + ps[u])[ls[u] & 1] =
-                in[u] ? ldr.commit((row0 + unsigned(ls[u])) * sy + unsigned(ps[u]), v[u]) : T(0);
+          if (el0 + u * B < W * N) {
+            const int slot = (ls[u] >> 1) * ld + ps[u];
+            T *aux = regK ? reinterpret_cast<T *>(bB + slot) + (ls[u] & 1) : nullptr;
+            reinterpret_cast<T *>(bA + slot)[ls[u] & 1] =
+                in[u] ? ldr.commit((row0 + unsigned(ls[u])) * sy + unsigned(ps[u]), v[u], aux) : T(0);
+          }
       }
     } else {
       const int l = threadIdx.x & (W - 1);
@@ -285,6 +314,7 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse
       const unsigned step = A == 1 ? sy : sz;
       const int pstep = B >> lgW;
       T *col = reinterpret_cast<T *>(bA + (l >> 1) * ld) + (l & 1);
+      T *acol = regK ? reinterpret_cast<T *>(bB + (l >> 1) * ld) + (l & 1) : nullptr;
       for (int q0 = threadIdx.x >> lgW; q0 < N; q0 += Load::U * pstep) {
         typename Load::V v[Load::U];
 #pragma unroll
@@ -295,7 +325,7 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse
 #pragma unroll
         for (int u = 0; u < Load::U; ++u) {
           const int pos = q0 + u * pstep;
-          if (pos < N) col[2 * pos] = ok ? ldr.commit(base + unsigned(pos) * step, v[u]) : T(0);
+          if (pos < N) col[2 * pos] = ok ? ldr.commit(base + unsigned(pos) * step, v[u], acol ? acol + 2 * pos : nullptr) : T(0);
         }
       }
     }
@@ -356,7 +386,8 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse
       for (int el = threadIdx.x; el < W * N; el += B) {
         if (row0 + unsigned(l) < nlines) {
           const Split<T> sp = pair_split(in + (l >> 1) * ld, N, pos);
-          store((row0 + unsigned(l)) * sy + unsigned(pos), (l & 1) ? sp.bk : sp.ak);
+          const T *aux = regK ? reinterpret_cast<const T *>(bB + (l >> 1) * ld + pos) + (l & 1) : nullptr;
+          store((row0 + unsigned(l)) * sy + unsigned(pos), (l & 1) ? sp.bk : sp.ak, aux);
         }
         pos += dp;
         l += dl;
@@ -370,9 +401,10 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse
       if (x0 + l < g.nx) {
         const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x0 + l);
         const unsigned step = A == 1 ? sy : sz;
+        const T *acol = regK ? reinterpret_cast<const T *>(bB + (l >> 1) * ld) + (l & 1) : nullptr;
         for (int pos = threadIdx.x >> lgW; pos < N; pos += B >> lgW) {
           const Split<T> sp = pair_split(in + (l >> 1) * ld, N, pos);
-          store(base + unsigned(pos) * step, (l & 1) ? sp.bk : sp.ak);
+          store(base + unsigned(pos) * step, (l & 1) ? sp.bk : sp.ak, acol ? acol + 2 * pos : nullptr);
         }
       }
     }
@@ -655,10 +687,7 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
       tile_pass<T>(a, sm, 1, false, lw, StoreW<T>{a.w});
       if (!tm.sync()) return;
       CgAcc<T> srz;
-      tile_pass<T>(a, sm, 0, false, lw, [&](unsigned i, T v) {
-        a.w[i] = v;
-        srz.add(a.r[i] * v);
-      });
+      tile_pass<T>(a, sm, 0, false, LoadWR<T>{a.w, a.r}, StoreRZ<T>{a.w, a.r, &srz});
       {
         const double v = block_sum_n(srz.get(), sh);
         if (threadIdx.x == 0) pa.part[blockIdx.x] = v;
