@@ -62,6 +62,7 @@ template <typename T> struct SArgs {
   T *r, *p, *q, *e, *w;
   T inv_eref_n;      // 1 / (eps_ref N)
   int ncode, ntw, ns;  // lengths of the shared-memory tables (all axes)
+  int xbulk;           // x passes by bulk copies (x lines transformed in registers)
 };
 
 // Per-thread sums of the conjugate-gradient scalars (r.r, r.z, p.q, sum e):
@@ -94,7 +95,7 @@ template <typename T> struct Smem {
   C2<T> *tw;
   T *sym;
   C2<T> *lanetw;  // [3][32][kLaneTw]
-  C2<T> *bA;      // tile buffers (the second one follows the first)
+  C2<T> *bA;      // four tile buffers, one after the other
 };
 template <typename T> __device__ Smem<T> smem_layout(unsigned char *raw, const SArgs<T> &a) {
   Smem<T> m;
@@ -278,88 +279,127 @@ __device__ __forceinline__ void reg_line_pair(C2<T> *X, int mode, const C2<T> *l
   for (int k = 0; k < K; ++k) X[lane + 32 * k] = C2<T>{ha[k], hb[k]};
 }
 
-// Staging functors, one line pair element (a, b) at a time: fetch() issues
-// the global loads (no stores, so a chunk's loads are all in flight
-// together), commit() finishes the element and returns the packed value
-// a + i b.  Line b may be missing (hb false).  The aux slot is the element's
-// place in the second tile buffer when the lines are transformed in place
-// (register transform), else null: a pass can keep a second pair of values
-// there for its store.
-template <typename T> struct LoadW {
-  static constexpr int U = kU / 2;
-  const T *w;
-  struct V {
-    T a, b;
-  };
-  __device__ __forceinline__ V fetch(unsigned ia, unsigned ib, bool hb) const { return V{w[ia], hb ? w[ib] : T(0)}; }
-  __device__ __forceinline__ C2<T> commit(unsigned, unsigned, bool, const V &v, C2<T> *) const {
-    return C2<T>{v.a, v.b};
+// adjacent pair (p[i], p[i + 1]) as one aligned vector access (i even)
+template <typename T> struct Vec2T;
+template <> struct Vec2T<float> {
+  using t = float2;
+};
+template <> struct Vec2T<double> {
+  using t = double2;
+};
+template <typename T> __device__ __forceinline__ void st_pair(T *p, unsigned i, C2<T> v) {
+  typename Vec2T<T>::t o;
+  o.x = v.x;
+  o.y = v.y;
+  *reinterpret_cast<typename Vec2T<T>::t *>(p + i) = o;
+}
+
+// Asynchronous copies global -> shared (no registers held while in flight):
+// one element, or an aligned adjacent pair into one packed slot.
+template <typename T> __device__ __forceinline__ void cp_one(T *dst, const T *src) {
+  const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+template <typename T> __device__ __forceinline__ void cp_pair(C2<T> *dst, const T *src) {
+  const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+// line pair (a at ia, b at ib or missing) of array p into packed slot d
+template <typename T>
+__device__ __forceinline__ void cp_line_pair(C2<T> *d, const T *p, unsigned ia, unsigned ib, bool hb, bool adj) {
+  if (adj) {
+    cp_pair(d, p + ia);
+    return;
   }
+  cp_one(&d->x, p + ia);
+  if (hb) cp_one(&d->y, p + ib);
+  else d->y = T(0);
+}
+
+// Tile buffers of a pass: packed line pairs (a + i b) at slot m * ld + pos.
+// bA receives the values to transform (and holds the result), bB is the
+// aux / ping-pong buffer, bC and bD stage the update's e and p.
+template <typename T> struct Bufs {
+  C2<T> *A, *B, *C, *D;
+  C2<T> *X;  // aux slots (bB) when the lines are transformed in place, else null
+};
+
+// Staging functors of one line-pair element: stage() issues the asynchronous
+// copies into the tile buffers (line b may be missing: hb false; adj: b is
+// the element after a and the pair is aligned, one vector copy); finish()
+// runs after the copies have landed and forms the value to transform in bA.
+// A pass that needs a second pair of values at its store keeps them in the
+// aux slots (register transforms only: the plan stages use bB).
+template <typename T> struct LoadW {
+  static constexpr bool kFinish = false;
+  const T *w;
+  __device__ __forceinline__ void stage(unsigned ia, unsigned ib, bool hb, bool adj, const Bufs<T> &b, int s) const {
+    cp_line_pair(b.A + s, w, ia, ib, hb, adj);
+  }
+  __device__ __forceinline__ void finish(unsigned, unsigned, bool, const Bufs<T> &, int) const {}
 };
 // stages w and keeps r in the aux slot (the last x pass: r.z at the store)
 template <typename T> struct LoadWR {
-  static constexpr int U = kU / 4;
+  static constexpr bool kFinish = false;
   const T *w, *r;
-  struct V {
-    T wa, wb, ra, rb;
-  };
-  __device__ __forceinline__ V fetch(unsigned ia, unsigned ib, bool hb) const {
-    return V{w[ia], hb ? w[ib] : T(0), r[ia], hb ? r[ib] : T(0)};
+  __device__ __forceinline__ void stage(unsigned ia, unsigned ib, bool hb, bool adj, const Bufs<T> &b, int s) const {
+    cp_line_pair(b.A + s, w, ia, ib, hb, adj);
+    if (b.X) cp_line_pair(b.X + s, r, ia, ib, hb, adj);
   }
-  __device__ __forceinline__ C2<T> commit(unsigned, unsigned, bool, const V &v, C2<T> *aux) const {
-    if (aux) *aux = C2<T>{v.ra, v.rb};
-    return C2<T>{v.wa, v.wb};
-  }
+  __device__ __forceinline__ void finish(unsigned, unsigned, bool, const Bufs<T> &, int) const {}
 };
 // r -= alpha q and e += alpha p (upd), sums of r^2 and e; stages r
 template <typename T> struct LoadU {
-  static constexpr int U = kU / 4;
+  static constexpr bool kFinish = true;
   T *r, *e;
   const T *q, *p;
   T al;
   bool upd, he;
   CgAcc<T> *sr, *se;
-  struct One {
-    T r, q, e, p;
-  };
-  struct V {
-    One a, b;
-  };
-  __device__ __forceinline__ One one(unsigned i) const {
-    One v;
-    v.r = r[i];
-    v.q = upd ? q[i] : T(0);
-    v.e = upd && he ? e[i] : T(0);
-    v.p = upd ? p[i] : T(0);
-    return v;
-  }
-  __device__ __forceinline__ V fetch(unsigned ia, unsigned ib, bool hb) const {
-    V v;
-    v.a = one(ia);
-    v.b = hb ? one(ib) : One{T(0), T(0), T(0), T(0)};
-    return v;
-  }
-  __device__ __forceinline__ T fin(unsigned i, const One &v) const {
-    T rv = v.r;
+  __device__ __forceinline__ void stage(unsigned ia, unsigned ib, bool hb, bool adj, const Bufs<T> &b, int s) const {
+    cp_line_pair(b.A + s, (const T *)r, ia, ib, hb, adj);
     if (upd) {
-      rv -= al * v.q;
+      cp_line_pair(b.B + s, q, ia, ib, hb, adj);
+      cp_line_pair(b.D + s, p, ia, ib, hb, adj);
+      if (he) cp_line_pair(b.C + s, (const T *)e, ia, ib, hb, adj);
+    }
+  }
+  __device__ __forceinline__ T fin(unsigned i, T rv, T qv, T ev, T pv) const {
+    if (upd) {
+      rv -= al * qv;
       r[i] = rv;
-      const T ev = v.e + al * v.p;
-      e[i] = ev;
-      se->add(ev);
+      const T en = ev + al * pv;
+      e[i] = en;
+      se->add(en);
     }
     sr->add(rv * rv);
     return rv;
   }
-  __device__ __forceinline__ C2<T> commit(unsigned ia, unsigned ib, bool hb, const V &v, C2<T> *) const {
-    const T ra = fin(ia, v.a);
-    const T rb = hb ? fin(ib, v.b) : T(0);
-    return C2<T>{ra, rb};
+  __device__ __forceinline__ void finish(unsigned ia, unsigned ib, bool hb, const Bufs<T> &b, int s) const {
+    const C2<T> rv = b.A[s];
+    const C2<T> qv = upd ? b.B[s] : C2<T>{T(0), T(0)};
+    const C2<T> pv = upd ? b.D[s] : C2<T>{T(0), T(0)};
+    const C2<T> ev = upd && he ? b.C[s] : C2<T>{T(0), T(0)};
+    const T ra = fin(ia, rv.x, qv.x, ev.x, pv.x);
+    const T rb = hb ? fin(ib, rv.y, qv.y, ev.y, pv.y) : T(0);
+    b.A[s] = C2<T>{ra, rb};
   }
 };
 template <typename T> struct StoreW {
   T *w;
-  __device__ __forceinline__ void operator()(unsigned ia, unsigned ib, bool hb, C2<T> v, const C2<T> *) const {
+  __device__ __forceinline__ void operator()(unsigned ia, unsigned ib, bool hb, bool adj, C2<T> v,
+                                             const C2<T> *) const {
+    if (adj) {
+      st_pair(w, ia, v);
+      return;
+    }
     w[ia] = v.x;
     if (hb) w[ib] = v.y;
   }
@@ -369,7 +409,8 @@ template <typename T> struct StoreRZ {
   T *w;
   const T *r;
   CgAcc<T> *acc;
-  __device__ __forceinline__ void operator()(unsigned ia, unsigned ib, bool hb, C2<T> v, const C2<T> *aux) const {
+  __device__ __forceinline__ void operator()(unsigned ia, unsigned ib, bool hb, bool, C2<T> v,
+                                             const C2<T> *aux) const {
     w[ia] = v.x;
     acc->add((aux ? aux->x : r[ia]) * v.x);
     if (hb) {
@@ -380,7 +421,8 @@ template <typename T> struct StoreRZ {
 };
 
 // One lattice pass along axis A over every tile owned by this block: stage
-// the tile's line pairs through `ld`, transform them (mode: forward, inverse,
+// the tile's line pairs through `ldr` (asynchronous copies, all in flight
+// together), transform them (mode: forward, inverse,
 // or forward + symbol scaling + inverse), write through `store`.  Each thread
 // stages and stores whole line pairs (a, b): the packed value a + i b is one
 // shared-memory word.  Axes of length 32 K (K = 1, 2, 4, 8) are transformed
@@ -422,22 +464,45 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, int mode,
     const int o = A == 0 ? 0 : t / xt;
     const int x0 = A == 0 ? 0 : (t - o * xt) << lgW;
     const unsigned row0 = unsigned(t) << lgW;
-    // staging in chunks of Load::U pairs per thread: all loads of a chunk are
-    // issued before the chunk is finished and stored (latency hiding)
+    // staging: every copy of the tile in flight at once (asynchronous copies
+    // into the packed slots), then the functor's arithmetic on the tile
+    const Bufs<T> bufs{bA, bB, bB + pairs * ld, bB + 2 * pairs * ld, regK ? bB : nullptr};
     if (A == 0) {
       int m = m0, pos = q0;
-      for (int e0 = threadIdx.x; e0 < E; e0 += Load::U * B) {
-        typename Load::V v[Load::U];
-        int ms[Load::U], ps[Load::U];
-        bool in[Load::U], hb[Load::U];
-#pragma unroll
-        for (int u = 0; u < Load::U; ++u) {
-          ms[u] = m;
-          ps[u] = pos;
+      for (int e = threadIdx.x; e < E; e += B) {
+        const unsigned ra = row0 + 2u * unsigned(m);
+        if (ra < nlines)
+          ldr.stage(ra * sy + unsigned(pos), (ra + 1u) * sy + unsigned(pos), ra + 1u < nlines, false, bufs,
+                    m * ld + pos);
+        else
+          bA[m * ld + pos] = C2<T>{T(0), T(0)};
+        pos += dq;
+        m += dm;
+        if (pos >= N) {
+          pos -= N;
+          ++m;
+        }
+      }
+    } else {
+      const int x = x0 + 2 * myp;
+      const bool va = x < g.nx, vb = x + 1 < g.nx;
+      const bool adj = (g.nx & 1) == 0;  // even rows: every pair (x, x + 1) is aligned
+      const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x);
+      for (int pos = myq; pos < N; pos += qstep) {
+        const unsigned i = base + unsigned(pos) * step;
+        if (va) ldr.stage(i, i + 1u, vb, adj, bufs, myp * ld + pos);
+        else bA[myp * ld + pos] = C2<T>{T(0), T(0)};
+      }
+    }
+    cp_wait_all();
+    __syncthreads();
+    if (Load::kFinish) {
+      if (A == 0) {
+        int m = m0, pos = q0;
+        for (int e = threadIdx.x; e < E; e += B) {
           const unsigned ra = row0 + 2u * unsigned(m);
-          in[u] = e0 + u * B < E && ra < nlines;
-          hb[u] = ra + 1u < nlines;
-          if (in[u]) v[u] = ldr.fetch(ra * sy + unsigned(pos), (ra + 1u) * sy + unsigned(pos), hb[u]);
+          if (ra < nlines)
+            ldr.finish(ra * sy + unsigned(pos), (ra + 1u) * sy + unsigned(pos), ra + 1u < nlines, bufs, m * ld + pos);
           pos += dq;
           m += dm;
           if (pos >= N) {
@@ -445,43 +510,18 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, int mode,
             ++m;
           }
         }
-#pragma unroll
-        for (int u = 0; u < Load::U; ++u)
-          if (e0 + u * B < E) {
-            const int slot = ms[u] * ld + ps[u];
-            const unsigned ra = row0 + 2u * unsigned(ms[u]);
-            bA[slot] = in[u] ? ldr.commit(ra * sy + unsigned(ps[u]), (ra + 1u) * sy + unsigned(ps[u]), hb[u], v[u],
-                                          regK ? bB + slot : nullptr)
-                             : C2<T>{T(0), T(0)};
-          }
-      }
-    } else {
-      const int x = x0 + 2 * myp;
-      const bool va = x < g.nx, vb = x + 1 < g.nx;
-      const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x);
-      C2<T> *col = bA + myp * ld;
-      C2<T> *acol = regK ? bB + myp * ld : nullptr;
-      for (int p0 = myq; p0 < N; p0 += Load::U * qstep) {
-        typename Load::V v[Load::U];
-#pragma unroll
-        for (int u = 0; u < Load::U; ++u) {
-          const int pos = p0 + u * qstep;
-          if (va && pos < N) {
+      } else {
+        const int x = x0 + 2 * myp;
+        if (x < g.nx) {
+          const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x);
+          for (int pos = myq; pos < N; pos += qstep) {
             const unsigned i = base + unsigned(pos) * step;
-            v[u] = ldr.fetch(i, i + 1u, vb);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < Load::U; ++u) {
-          const int pos = p0 + u * qstep;
-          if (pos < N) {
-            const unsigned i = base + unsigned(pos) * step;
-            col[pos] = va ? ldr.commit(i, i + 1u, vb, v[u], acol ? acol + pos : nullptr) : C2<T>{T(0), T(0)};
+            ldr.finish(i, i + 1u, x + 1 < g.nx, bufs, myp * ld + pos);
           }
         }
       }
+      __syncthreads();
     }
-    __syncthreads();
     const C2<T> *res = bA;  // the transformed line pairs
     if (regK) {
       const C2<T> *lt = sm.lanetw + (A * 32 + lane) * kLaneTw;
@@ -563,7 +603,7 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, int mode,
       for (int e = threadIdx.x; e < E; e += B) {
         const unsigned ra = row0 + 2u * unsigned(m);
         if (ra < nlines)
-          store(ra * sy + unsigned(pos), (ra + 1u) * sy + unsigned(pos), ra + 1u < nlines, value(m, pos),
+          store(ra * sy + unsigned(pos), (ra + 1u) * sy + unsigned(pos), ra + 1u < nlines, false, value(m, pos),
                 regK ? bB + m * ld + pos : nullptr);
         pos += dq;
         m += dm;
@@ -576,14 +616,197 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, int mode,
       const int x = x0 + 2 * myp;
       if (x < g.nx) {
         const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x);
-        const bool vb = x + 1 < g.nx;
+        const bool vb = x + 1 < g.nx, adj = (g.nx & 1) == 0;
         for (int pos = myq; pos < N; pos += qstep) {
           const unsigned i = base + unsigned(pos) * step;
-          store(i, i + 1u, vb, value(myp, pos), regK ? bB + myp * ld + pos : nullptr);
+          store(i, i + 1u, vb, adj, value(myp, pos), regK ? bB + myp * ld + pos : nullptr);
         }
       }
     }
     __syncthreads();
+  }
+}
+
+// ---- x passes with bulk copies --------------------------------------------
+// A tile of the x pass is W consecutive rows: one contiguous block of W nx
+// words of every array.  When the x lines are transformed in registers, the
+// tile moves by single bulk copies (cp.async.bulk, completion counted on an
+// mbarrier) into row-major tile buffers, and the results leave by bulk
+// stores; only the arithmetic touches the tile element by element.
+// Proxy fences order the bulk copies (async proxy) against the ordinary
+// loads and stores of this block and, through the grid barrier, of the
+// others.
+constexpr long long kCopyWaitLimit = 1ll << 24;  // polls of a copy's mbarrier before giving up
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return unsigned(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(unsigned long long *m) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long *m, unsigned bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(m)),
+               "r"(bytes)
+               : "memory");
+}
+// bounded wait for the completion of the mbarrier phase of parity `par`
+__device__ __forceinline__ bool mbar_wait(unsigned long long *m, unsigned par, long long limit) {
+  for (long long k = 0; k < limit; ++k) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(m)), "r"(par)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+struct BulkSync {
+  unsigned long long *mbar;  // the block's copy mbarrier
+  unsigned phase;            // parity of its next phase
+  Bar *bar;                  // grid barrier (abort flag)
+  int *status;
+};
+
+enum XKind { kXUpdate = 0, kXForward = 1, kXInverse = 2 };
+
+// One x pass over this block's tiles with bulk copies (K = nx / 32):
+//   kXUpdate   r -= alpha q, e += alpha p (upd), sums of r^2 (s1) and e (s2),
+//              forward transform of r into w;
+//   kXForward  forward transform of r into w;
+//   kXInverse  inverse transform of w (z = M^-1 r) and the sum r.z (s1).
+// Buffers: B0 r (or w), B1 q (then the transform's output) or r, B2 e, B3 p.
+// Returns false (abort flag and status raised) when a copy does not land.
+template <typename T, int K>
+__device__ bool x_pass_bulk(const SArgs<T> &a, const Smem<T> &sm, int kind, T al, bool upd, bool he, CgAcc<T> &s1,
+                            CgAcc<T> &s2, BulkSync &bs) {
+  __shared__ int copy_ok;
+  const Grid3 g = a.g;
+  const int W = a.ax[0].W, lgW = a.ax[0].lgW, N = g.nx;
+  const unsigned nlines = unsigned(g.ny) * unsigned(g.nz);
+  const int nt = int((nlines + unsigned(W) - 1u) >> lgW);
+  const int tile = W * N, B = blockDim.x;
+  T *B0 = reinterpret_cast<T *>(sm.bA), *B1 = B0 + tile, *B2 = B1 + tile, *B3 = B2 + tile;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const C2<T> *lt = sm.lanetw + lane * kLaneTw;
+  if (threadIdx.x == 0) fence_async_global();  // earlier phases' stores before the bulk reads
+  for (int t = blockIdx.x; t < nt; t += gridDim.x) {
+    const unsigned row0 = unsigned(t) << lgW;
+    const int rows = min(W, int(nlines - row0));
+    const size_t off = size_t(row0) * size_t(N);
+    const unsigned bytes = unsigned(rows) * unsigned(N) * unsigned(sizeof(T));
+    if (threadIdx.x == 0) bulk_wait_read();  // the previous tile's bulk stores have read their buffers
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      fence_async_shared();
+      const bool lq = kind == kXUpdate && upd, le = lq && he;
+      const unsigned nbuf = 1u + (kind == kXInverse ? 1u : 0u) + (lq ? 2u : 0u) + (le ? 1u : 0u);
+      mbar_expect(bs.mbar, nbuf * bytes);
+      bulk_load(B0, (kind == kXInverse ? a.w : a.r) + off, bytes, bs.mbar);
+      if (kind == kXInverse) bulk_load(B1, a.r + off, bytes, bs.mbar);
+      if (lq) {
+        bulk_load(B1, a.q + off, bytes, bs.mbar);
+        bulk_load(B3, a.p + off, bytes, bs.mbar);
+      }
+      if (le) bulk_load(B2, a.e + off, bytes, bs.mbar);
+    }
+    for (int e = rows * N + threadIdx.x; e < tile; e += B) B0[e] = T(0);  // line b past the last row
+    if (threadIdx.x == 0) {
+      copy_ok = mbar_wait(bs.mbar, bs.phase, kCopyWaitLimit);
+      if (!copy_ok) {
+        atomicExch(&bs.bar->abort, 1);
+        atomicOr(bs.status, ST_TIMEOUT);
+        mbar_wait(bs.mbar, bs.phase, kCopyWaitLimit);  // let the copies land before the block leaves
+      }
+    }
+    bs.phase ^= 1u;
+    __syncthreads();
+    if (!copy_ok) {
+      if (threadIdx.x == 0) bulk_wait_all();
+      return false;
+    }
+    if (kind == kXUpdate) {
+      for (int e = threadIdx.x; e < rows * N; e += B) {
+        T rv = B0[e];
+        if (upd) {
+          rv -= al * B1[e];
+          B0[e] = rv;
+          const T ev = (he ? B2[e] : T(0)) + al * B3[e];
+          B2[e] = ev;
+          s2.add(ev);
+        }
+        s1.add(rv * rv);
+      }
+      fence_async_shared();
+      __syncthreads();
+      if (upd && threadIdx.x == 0) {
+        bulk_store(a.r + off, B0, bytes);
+        bulk_store(a.e + off, B2, bytes);
+        bulk_commit();
+      }
+    }
+    // the line pairs (rows 2m, 2m + 1) in registers, one warp per pair
+    T *dst = kind == kXInverse ? B0 : B1;
+    for (int m = warp; m < (W >> 1); m += nw) {
+      const T *ra = B0 + 2 * m * N, *rb = ra + N;
+      C2<T> v[K];
+      T ha[K], hb[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = C2<T>{ra[lane + 32 * k], rb[lane + 32 * k]};
+      if (kind == kXInverse) {
+        dit_regs<T, K>(v, lt, lane);
+        split_nat<T, K>(v, lane, ha, hb);
+      } else {
+        dif_regs<T, K>(v, lt, lane);
+        split_perm<T, K>(v, lane, ha, hb);
+      }
+      T *da = dst + 2 * m * N, *db = da + N;
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        da[lane + 32 * k] = ha[k];
+        db[lane + 32 * k] = hb[k];
+      }
+    }
+    __syncthreads();
+    if (kind == kXInverse)
+      for (int e = threadIdx.x; e < rows * N; e += B) s1.add(B1[e] * B0[e]);
+    fence_async_shared();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      bulk_store(a.w + off, dst, bytes);
+      bulk_commit();
+    }
+  }
+  if (threadIdx.x == 0) {
+    bulk_wait_all();
+    fence_async_global();  // the bulk stores before the grid barrier's release
+  }
+  return true;
+}
+template <typename T>
+__device__ bool x_pass_bulk_k(const SArgs<T> &a, const Smem<T> &sm, int kind, T al, bool upd, bool he, CgAcc<T> &s1,
+                              CgAcc<T> &s2, BulkSync &bs) {
+  switch (reg_fft_k(a.g.nx)) {
+    case 1: return x_pass_bulk<T, 1>(a, sm, kind, al, upd, he, s1, s2, bs);
+    case 2: return x_pass_bulk<T, 2>(a, sm, kind, al, upd, he, s1, s2, bs);
+    case 4: return x_pass_bulk<T, 4>(a, sm, kind, al, upd, he, s1, s2, bs);
+    default: return x_pass_bulk<T, 8>(a, sm, kind, al, upd, he, s1, s2, bs);
   }
 }
 
@@ -723,20 +946,34 @@ __device__ void residual_cells(const SArgs<T> &a, double qbar, DF qbar_df, doubl
 #pragma unroll
       for (int k = 0; k < 6; ++k) kf[k] = T(0.5) * (ev[u][0] + ev[u][k + 1]);
       if constexpr (DFM) {
-        const DF p{ph[u][0], pl[u][0]};
-        DF Ap = df_mul_f(df_sub(DF{ph[u][1], pl[u][1]}, p), kf[0]);
+        // sum_k kf_k (phi_k - phi_0): each difference is the exact difference
+        // of the high words (two_sum) plus the difference of the low words;
+        // the high part of kf_k d_k is exact with its FMA error term, the high
+        // parts are summed with compensation and the low parts in FP32
+        // (error about 2^-46 of the largest flux term, as in double-float
+        // arithmetic)
+        float ahi = 0.f, alo = 0.f;
 #pragma unroll
-        for (int k = 1; k < 6; ++k) Ap = df_add(Ap, df_mul_f(df_sub(DF{ph[u][k + 1], pl[u][k + 1]}, p), kf[k]));
-        DF b = df_sub(qbar_df, DF{float(qv[u]), 0.f});
+        for (int k = 0; k < 6; ++k) {
+          const DF d = two_sum(ph[u][k + 1], -ph[u][0]);
+          const float dlo = __fadd_rn(d.lo, __fsub_rn(pl[u][k + 1], pl[u][0]));
+          const float prod = __fmul_rn(d.hi, kf[k]);
+          const float plo = __fmaf_rn(dlo, kf[k], __fmaf_rn(d.hi, kf[k], -prod));
+          const DF t = two_sum(ahi, prod);
+          ahi = t.hi;
+          alo = __fadd_rn(alo, __fadd_rn(t.lo, plo));
+        }
+        DF b = two_sum(qbar_df.hi, -float(qv[u]));
+        b.lo = __fadd_rn(b.lo, qbar_df.lo);
         if (pa.edf[0].hi != 0.f) b = df_add(b, df_mul(pa.edf[0], two_sum(kf[0], -kf[1])));
         if (pa.edf[1].hi != 0.f) b = df_add(b, df_mul(pa.edf[1], two_sum(kf[2], -kf[3])));
         if (pa.edf[2].hi != 0.f) b = df_add(b, df_mul(pa.edf[2], two_sum(kf[4], -kf[5])));
-        const DF r = df_sub(b, Ap);
-        const float rf = __fadd_rn(r.hi, r.lo);
+        const DF r = two_sum(b.hi, -ahi);
+        const float rf = __fadd_rn(r.hi, __fadd_rn(r.lo, __fsub_rn(b.lo, alo)));
         L0.b[c[u].i] = T(rf);
         sr.add(rf * rf);
         sb.add(b.hi * b.hi);
-        sp.add(p.hi);
+        sp.add(ph[u][0]);
       } else {
         const double p = ph[u][0];
         double b = -(double(qv[u]) - qbar);
@@ -763,7 +1000,9 @@ template <typename T, bool DFM>
 __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[kSB];
+  __shared__ unsigned long long mbar;
   const Smem<T> sm = smem_layout<T>(smem_raw, a);
+  if (threadIdx.x == 0) mbar_init(&mbar);
   load_tables(a, sm);
   const PArgs<T> &pa = a.pa;
   const GridTeam tm{pa.bar, pa.status, pa.spin_limit};
@@ -774,6 +1013,7 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   const int nb = tm.nblocks();
   PDev *st = pa.st;
   const int have_prev = st->have_prev;
+  BulkSync bs{&mbar, 0u, pa.bar, pa.status};
 
   // initial guess 2 phi(t-1) - phi(t-2), sum of q (kU cells per thread in flight)
   SumAcc<DFM> sq;
@@ -875,6 +1115,8 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
       const bool upd = !first, he = have_e;
       if (last) {
         update_cells<T>(a, al, he, sr, se);
+      } else if (a.xbulk) {
+        x_pass_bulk_k<T>(a, sm, kXUpdate, al, upd, he, sr, se, bs);
       } else {
         LoadU<T> lu{a.r, a.e, a.q, a.p, al, upd, he, &sr, &se};
         tile_pass<T>(a, sm, 0, kFwd, lu, StoreW<T>{a.w});
@@ -899,7 +1141,12 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
       }
       if (last) {
         // mispredicted: the x pass of the updated r
-        tile_pass<T>(a, sm, 0, kFwd, LoadW<T>{a.r}, StoreW<T>{a.w});
+        if (a.xbulk) {
+          CgAcc<T> d0, d1;
+          x_pass_bulk_k<T>(a, sm, kXForward, T(0), false, false, d0, d1, bs);
+        } else {
+          tile_pass<T>(a, sm, 0, kFwd, LoadW<T>{a.r}, StoreW<T>{a.w});
+        }
         if (!tm.sync()) return;
       }
       // preconditioner: Y, Z (scale), Y, X passes on w
@@ -911,7 +1158,12 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
       tile_pass<T>(a, sm, 1, kInv, lw, StoreW<T>{a.w});
       if (!tm.sync()) return;
       CgAcc<T> srz;
-      tile_pass<T>(a, sm, 0, kInv, LoadWR<T>{a.w, a.r}, StoreRZ<T>{a.w, a.r, &srz});
+      if (a.xbulk) {
+        CgAcc<T> d1;
+        x_pass_bulk_k<T>(a, sm, kXInverse, T(0), false, false, srz, d1, bs);
+      } else {
+        tile_pass<T>(a, sm, 0, kInv, LoadWR<T>{a.w, a.r}, StoreRZ<T>{a.w, a.r, &srz});
+      }
       {
         const double v = block_sum_n(srz.get(), sh);
         if (threadIdx.x == 0) pa.part[blockIdx.x] = v;
@@ -1070,7 +1322,7 @@ template <typename T> static bool spectral_setup(Spectral *s, const Dims &d) {
     }
     s->W[A] = W;
     s->lgW[A] = lg;
-    tiles = std::max(tiles, 2 * (size_t)(W / 2) * (n + 1) * sizeof(C2<T>));
+    tiles = std::max(tiles, 4 * (size_t)(W / 2) * (n + 1) * sizeof(C2<T>));
     // symbols 2 (1 - cos(2 pi k / n)) in the axis's storage order: slot
     // l + 32 kappa of a register-transformed axis holds frequency
     // kappa + K bitrev5(l)
@@ -1166,6 +1418,8 @@ template <typename T, bool DFM> static int launch(Spectral *s, const Ctx &c, con
   a.e = (T *)s->e;
   a.w = (T *)s->w;
   a.inv_eref_n = T(1.0 / (s->eps_ref * double(c.d.N)));
+  // rows of nx words start on 16-byte boundaries (cudaMalloc'd arrays)
+  a.xbulk = reg_fft_k(c.d.nx) != 0 && (c.d.nx * sizeof(T)) % 16 == 0;
   if (cudaMemsetAsync(pa.bar, 0, sizeof(Bar), st) != cudaSuccess) return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(s->grid);
