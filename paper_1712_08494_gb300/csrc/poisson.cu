@@ -10,7 +10,8 @@
 // the residual b - A phi is formed in FP64 against the FP64 potential, a
 // V(2,2) cycle in the compute type (FP32 or FP64) approximates the
 // correction, and phi is updated in FP64.  Cell-centred grids: coarse face
-// coefficients are means of the fine faces they cover, restriction averages
+// coefficients combine the fine faces in series along the face normal and
+// average them across it (coarse_coef), restriction averages
 // the children, prolongation is trilinear, smoothing is red-black
 // Gauss-Seidel (damped Jacobi where an axis is odd).  All levels of at most
 // kTailCells cells are cycled inside one thread block.
@@ -83,31 +84,16 @@ __global__ void k_coef0(Dims d, const T *__restrict__ eps, T *__restrict__ kx, T
   kz[i] = T(0.5) * (e + eps[site(d, x, y, wrapp(z, d.nz))]);
 }
 
-// coarse face (I + a/2) covers the fine faces (2I+1 + a/2) along a, averaged
-// over the transverse children
+// coarse face coefficients of one level from the finer one (coarse_coef)
 template <typename T> __global__ void k_coef_coarsen(Level<T> F, Level<T> C) {
-  const Dims f = F.dims(), c = C.dims();
+  const Dims c = C.dims();
   long long I = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (I >= c.N) return;
   int X, Y, Z;
   coords(c, I, X, Y, Z);
-  const int base[3] = {C.cf[0] ? 2 * X : X, C.cf[1] ? 2 * Y : Y, C.cf[2] ? 2 * Z : Z};
-  for (int a = 0; a < 3; ++a) {
-    T acc = T(0);
-    int cnt = 0;
-    const int ra = C.cf[a] ? 1 : 0;
-    const int b1 = (a + 1) % 3, b2 = (a + 2) % 3;
-    for (int t1 = 0; t1 <= C.cf[b1]; ++t1)
-      for (int t2 = 0; t2 <= C.cf[b2]; ++t2) {
-        int p[3];
-        p[a] = base[a] + ra;
-        p[b1] = base[b1] + t1;
-        p[b2] = base[b2] + t2;
-        acc += F.k[a][site(f, p[0], p[1], p[2])];
-        ++cnt;
-      }
-    C.k[a][I] = acc / T(cnt);
-  }
+  C.k[0][I] = coarse_coef<0>(F, C, X, Y, Z);
+  C.k[1][I] = coarse_coef<1>(F, C, X, Y, Z);
+  C.k[2][I] = coarse_coef<2>(F, C, X, Y, Z);
 }
 
 template <typename T> __global__ void __launch_bounds__(1024) k_tail(Tail<T> tl, int first) {

@@ -238,17 +238,33 @@ template <typename T> __device__ __forceinline__ T diag_n(const Level<T> &L, con
   return L.h[0] * (f.xp + f.xm) + L.h[1] * (f.yp + f.ym) + L.h[2] * (f.zp + f.zm);
 }
 
-// Coarse face coefficient along axis AX of coarse cell (X, Y, Z): the mean of
-// the fine face coefficients on that face (fine cells of the coarse cell's
-// block next to its +AX face).  Axis indices are compile-time constants, so
-// the small coordinate arrays stay in registers.
+// Coarse face coefficient along axis AX of coarse cell (X, Y, Z).  Along a
+// coarsened axis the flux between the centres of coarse cells X and X + 1
+// crosses three fine faces in series: half of the face inside X (fine 2X |
+// 2X+1), the shared face (2X+1 | 2X+2) and half of the face inside X + 1
+// (2X+2 | 2X+3); their series conductance over the two fine spacings is
+// 2 / (1/(2 k_in) + 1/k_shared + 1/(2 k_next)) -- the harmonic weighting that
+// keeps a jump of the permittivity inside a coarse cell from passing as the
+// arithmetic mean (fewer cycles on the colloid boxes).  Across the face the
+// fine paths are averaged.  Along an axis that is not coarsened the coarse
+// face is the fine face.  Axis indices are compile-time constants, so the
+// small coordinate arrays stay in registers.
 template <int AX, typename T>
 __device__ __forceinline__ T coarse_coef(const Level<T> &F, const Level<T> &C, int X, int Y, int Z) {
   constexpr int B1 = (AX + 1) % 3, B2 = (AX + 2) % 3;
   const Dims f = F.dims();
   const int fn[3] = {f.nx, f.ny, f.nz};
-  int p[3] = {C.cf[0] ? 2 * X : X, C.cf[1] ? 2 * Y : Y, C.cf[2] ? 2 * Z : Z};
-  if (C.cf[AX]) p[AX] += 1;
+  const int p[3] = {C.cf[0] ? 2 * X : X, C.cf[1] ? 2 * Y : Y, C.cf[2] ? 2 * Z : Z};
+  // fine face coefficient along AX at fine cell q (face q | q + AX)
+  auto kf = [&](const int (&q)[3]) -> T {
+    const unsigned fi = site32(f, q[0], q[1], q[2]);
+    if (F.eps) {
+      int r[3] = {q[0], q[1], q[2]};
+      r[AX] = r[AX] + 1 == fn[AX] ? 0 : r[AX] + 1;
+      return T(0.5) * (F.eps[fi] + F.eps[site32(f, r[0], r[1], r[2])]);
+    }
+    return F.k[AX][fi];
+  };
   T acc = T(0);
   int cnt = 0;
   for (int t1 = 0; t1 <= C.cf[B1]; ++t1)
@@ -256,13 +272,16 @@ __device__ __forceinline__ T coarse_coef(const Level<T> &F, const Level<T> &C, i
       int q[3] = {p[0], p[1], p[2]};
       q[B1] += t1;
       q[B2] += t2;
-      const unsigned fi = site32(f, q[0], q[1], q[2]);
-      if (F.eps) {
-        int r[3] = {q[0], q[1], q[2]};
-        r[AX] = r[AX] + 1 == fn[AX] ? 0 : r[AX] + 1;
-        acc += T(0.5) * (F.eps[fi] + F.eps[site32(f, r[0], r[1], r[2])]);
+      if (C.cf[AX]) {
+        const int x0 = q[AX];
+        const T k_in = kf(q);
+        q[AX] = x0 + 1;
+        const T k_sh = kf(q);
+        q[AX] = x0 + 2 == fn[AX] ? 0 : x0 + 2;
+        const T k_nx = kf(q);
+        acc += T(2) / (T(0.5) / k_in + T(1) / k_sh + T(0.5) / k_nx);
       } else {
-        acc += F.k[AX][fi];
+        acc += kf(q);
       }
       ++cnt;
     }

@@ -62,7 +62,7 @@ template <typename T> struct SArgs {
   T *r, *p, *q, *e, *w;
   T inv_eref_n;      // 1 / (eps_ref N)
   int ncode, ntw, ns;  // lengths of the shared-memory tables (all axes)
-  int xbulk;           // x passes by bulk copies (x lines transformed in registers)
+  int xrows;           // x passes on whole rows (x lines transformed in registers)
 };
 
 // Per-thread sums of the conjugate-gradient scalars (r.r, r.z, p.q, sum e):
@@ -77,6 +77,24 @@ template <typename T> struct CgAcc {
 
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
+// The blocks' sums of M per-thread values into part[m nb + blockIdx.x], and
+// after the grid barrier the M grid sums, added by every block in the same
+// fixed order (every block holds bitwise the same scalars and takes the same
+// branches).  One value at a time: measured faster than reducing M values
+// together at 128^3.
+template <int M> __device__ __forceinline__ void put_block_sums(double (&v)[M], double *part, int nb, double *sh) {
+  for (int m = 0; m < M; ++m) {
+    const double t = block_sum_n(v[m], sh);
+    if (threadIdx.x == 0) part[m * nb + blockIdx.x] = t;
+  }
+}
+template <int M>
+__device__ __forceinline__ bool sync_sums(const GridTeam &tm, double *part, int nb, double (&v)[M], double *sh) {
+  if (!tm.sync()) return false;
+  for (int m = 0; m < M; ++m) v[m] = sum_partials(part + m * nb, nb, sh);
+  return true;
+}
 
 // Shared memory of a block, loaded once per launch: the three axes' plans,
 // butterfly codes, twiddles and symbols; then the two tile buffers.
@@ -627,76 +645,39 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, int mode,
   }
 }
 
-// ---- x passes with bulk copies --------------------------------------------
+// ---- x passes on whole rows -----------------------------------------------
 // A tile of the x pass is W consecutive rows: one contiguous block of W nx
-// words of every array.  When the x lines are transformed in registers, the
-// tile moves by single bulk copies (cp.async.bulk, completion counted on an
-// mbarrier) into row-major tile buffers, and the results leave by bulk
-// stores; only the arithmetic touches the tile element by element.
-// Proxy fences order the bulk copies (async proxy) against the ordinary
-// loads and stores of this block and, through the grid barrier, of the
-// others.
-constexpr long long kCopyWaitLimit = 1ll << 24;  // polls of a copy's mbarrier before giving up
-
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return unsigned(__cvta_generic_to_shared(p)); }
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, unsigned long long *mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(mbar))
-               : "memory");
-}
-__device__ __forceinline__ void bulk_store(void *dst, const void *src, unsigned bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;\n" ::"l"(dst), "r"(smem_u32(src)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_async_global() { asm volatile("fence.proxy.async.global;\n" ::: "memory"); }
-__device__ __forceinline__ void mbar_init(unsigned long long *m) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(m)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect(unsigned long long *m, unsigned bytes) {
-  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(m)),
-               "r"(bytes)
-               : "memory");
-}
-// bounded wait for the completion of the mbarrier phase of parity `par`
-__device__ __forceinline__ bool mbar_wait(unsigned long long *m, unsigned par, long long limit) {
-  for (long long k = 0; k < limit; ++k) {
-    unsigned done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(m)), "r"(par)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-struct BulkSync {
-  unsigned long long *mbar;  // the block's copy mbarrier
-  unsigned phase;            // parity of its next phase
-  Bar *bar;                  // grid barrier (abort flag)
-  int *status;
+// words of every array.  When the x lines are transformed in registers the
+// tile is copied row-major into the tile buffers by 16-byte asynchronous
+// copies (every copy of the tile in flight at once), the arithmetic runs on
+// 16-byte packs, and the results leave by 16-byte stores.  All of it stays in
+// the generic proxy: no proxy fence is needed between the phases.
+template <typename T> struct alignas(16) Pack {
+  static constexpr int n = 16 / sizeof(T);
+  T v[n];
 };
+template <typename T> __device__ __forceinline__ void cp16(T *dst, const T *src) {
+  const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+// rows of nw words (nw * sizeof(T) a multiple of 16), global -> shared
+template <typename T> __device__ __forceinline__ void cp_rows(T *dst, const T *src, int nw) {
+  constexpr int P = Pack<T>::n;
+  for (int i = threadIdx.x; i < nw / P; i += blockDim.x) cp16(dst + i * P, src + i * P);
+}
 
 enum XKind { kXUpdate = 0, kXForward = 1, kXInverse = 2 };
 
-// One x pass over this block's tiles with bulk copies (K = nx / 32):
+// One x pass over this block's tiles (K = nx / 32):
 //   kXUpdate   r -= alpha q, e += alpha p (upd), sums of r^2 (s1) and e (s2),
 //              forward transform of r into w;
 //   kXForward  forward transform of r into w;
 //   kXInverse  inverse transform of w (z = M^-1 r) and the sum r.z (s1).
 // Buffers: B0 r (or w), B1 q (then the transform's output) or r, B2 e, B3 p.
-// Returns false (abort flag and status raised) when a copy does not land.
 template <typename T, int K>
-__device__ bool x_pass_bulk(const SArgs<T> &a, const Smem<T> &sm, int kind, T al, bool upd, bool he, CgAcc<T> &s1,
-                            CgAcc<T> &s2, BulkSync &bs) {
-  __shared__ int copy_ok;
+__device__ void x_pass_rows(const SArgs<T> &a, const Smem<T> &sm, int kind, T al, bool upd, bool he, CgAcc<T> &s1,
+                            CgAcc<T> &s2) {
+  constexpr int P = Pack<T>::n;
   const Grid3 g = a.g;
   const int W = a.ax[0].W, lgW = a.ax[0].lgW, N = g.nx;
   const unsigned nlines = unsigned(g.ny) * unsigned(g.nz);
@@ -705,61 +686,44 @@ __device__ bool x_pass_bulk(const SArgs<T> &a, const Smem<T> &sm, int kind, T al
   T *B0 = reinterpret_cast<T *>(sm.bA), *B1 = B0 + tile, *B2 = B1 + tile, *B3 = B2 + tile;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const C2<T> *lt = sm.lanetw + lane * kLaneTw;
-  if (threadIdx.x == 0) fence_async_global();  // earlier phases' stores before the bulk reads
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
     const unsigned row0 = unsigned(t) << lgW;
     const int rows = min(W, int(nlines - row0));
+    const int nwd = rows * N;  // words of the tile's rows
     const size_t off = size_t(row0) * size_t(N);
-    const unsigned bytes = unsigned(rows) * unsigned(N) * unsigned(sizeof(T));
-    if (threadIdx.x == 0) bulk_wait_read();  // the previous tile's bulk stores have read their buffers
+    const bool lq = kind == kXUpdate && upd;
+    cp_rows(B0, (kind == kXInverse ? a.w : a.r) + off, nwd);
+    if (kind == kXInverse) cp_rows(B1, a.r + off, nwd);
+    if (lq) {
+      cp_rows(B1, a.q + off, nwd);
+      cp_rows(B3, a.p + off, nwd);
+      if (he) cp_rows(B2, a.e + off, nwd);
+    }
+    for (int e = nwd + threadIdx.x; e < tile; e += B) B0[e] = T(0);  // line b past the last row
+    cp_wait_all();
     __syncthreads();
-    if (threadIdx.x == 0) {
-      fence_async_shared();
-      const bool lq = kind == kXUpdate && upd, le = lq && he;
-      const unsigned nbuf = 1u + (kind == kXInverse ? 1u : 0u) + (lq ? 2u : 0u) + (le ? 1u : 0u);
-      mbar_expect(bs.mbar, nbuf * bytes);
-      bulk_load(B0, (kind == kXInverse ? a.w : a.r) + off, bytes, bs.mbar);
-      if (kind == kXInverse) bulk_load(B1, a.r + off, bytes, bs.mbar);
-      if (lq) {
-        bulk_load(B1, a.q + off, bytes, bs.mbar);
-        bulk_load(B3, a.p + off, bytes, bs.mbar);
-      }
-      if (le) bulk_load(B2, a.e + off, bytes, bs.mbar);
-    }
-    for (int e = rows * N + threadIdx.x; e < tile; e += B) B0[e] = T(0);  // line b past the last row
-    if (threadIdx.x == 0) {
-      copy_ok = mbar_wait(bs.mbar, bs.phase, kCopyWaitLimit);
-      if (!copy_ok) {
-        atomicExch(&bs.bar->abort, 1);
-        atomicOr(bs.status, ST_TIMEOUT);
-        mbar_wait(bs.mbar, bs.phase, kCopyWaitLimit);  // let the copies land before the block leaves
-      }
-    }
-    bs.phase ^= 1u;
-    __syncthreads();
-    if (!copy_ok) {
-      if (threadIdx.x == 0) bulk_wait_all();
-      return false;
-    }
     if (kind == kXUpdate) {
-      for (int e = threadIdx.x; e < rows * N; e += B) {
-        T rv = B0[e];
+      for (int i = threadIdx.x; i < nwd / P; i += B) {
+        Pack<T> rv = reinterpret_cast<const Pack<T> *>(B0)[i];
         if (upd) {
-          rv -= al * B1[e];
-          B0[e] = rv;
-          const T ev = (he ? B2[e] : T(0)) + al * B3[e];
-          B2[e] = ev;
-          s2.add(ev);
+          const Pack<T> qv = reinterpret_cast<const Pack<T> *>(B1)[i];
+          const Pack<T> pv = reinterpret_cast<const Pack<T> *>(B3)[i];
+          Pack<T> ev{};
+          if (he) ev = reinterpret_cast<const Pack<T> *>(B2)[i];
+#pragma unroll
+          for (int j = 0; j < P; ++j) {
+            rv.v[j] -= al * qv.v[j];
+            ev.v[j] += al * pv.v[j];
+            s2.add(ev.v[j]);
+          }
+          reinterpret_cast<Pack<T> *>(B0)[i] = rv;
+          reinterpret_cast<Pack<T> *>(a.r + off)[i] = rv;
+          reinterpret_cast<Pack<T> *>(a.e + off)[i] = ev;
         }
-        s1.add(rv * rv);
+#pragma unroll
+        for (int j = 0; j < P; ++j) s1.add(rv.v[j] * rv.v[j]);
       }
-      fence_async_shared();
       __syncthreads();
-      if (upd && threadIdx.x == 0) {
-        bulk_store(a.r + off, B0, bytes);
-        bulk_store(a.e + off, B2, bytes);
-        bulk_commit();
-      }
     }
     // the line pairs (rows 2m, 2m + 1) in registers, one warp per pair
     T *dst = kind == kXInverse ? B0 : B1;
@@ -784,33 +748,30 @@ __device__ bool x_pass_bulk(const SArgs<T> &a, const Smem<T> &sm, int kind, T al
       }
     }
     __syncthreads();
-    if (kind == kXInverse)
-      for (int e = threadIdx.x; e < rows * N; e += B) s1.add(B1[e] * B0[e]);
-    fence_async_shared();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      bulk_store(a.w + off, dst, bytes);
-      bulk_commit();
+    for (int i = threadIdx.x; i < nwd / P; i += B) {
+      const Pack<T> zv = reinterpret_cast<const Pack<T> *>(dst)[i];
+      reinterpret_cast<Pack<T> *>(a.w + off)[i] = zv;
+      if (kind == kXInverse) {
+        const Pack<T> rv = reinterpret_cast<const Pack<T> *>(B1)[i];
+#pragma unroll
+        for (int j = 0; j < P; ++j) s1.add(rv.v[j] * zv.v[j]);
+      }
     }
+    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    bulk_wait_all();
-    fence_async_global();  // the bulk stores before the grid barrier's release
-  }
-  return true;
 }
 template <typename T>
-__device__ bool x_pass_bulk_k(const SArgs<T> &a, const Smem<T> &sm, int kind, T al, bool upd, bool he, CgAcc<T> &s1,
-                              CgAcc<T> &s2, BulkSync &bs) {
+__device__ void x_pass_rows_k(const SArgs<T> &a, const Smem<T> &sm, int kind, T al, bool upd, bool he, CgAcc<T> &s1,
+                              CgAcc<T> &s2) {
   switch (reg_fft_k(a.g.nx)) {
-    case 1: return x_pass_bulk<T, 1>(a, sm, kind, al, upd, he, s1, s2, bs);
-    case 2: return x_pass_bulk<T, 2>(a, sm, kind, al, upd, he, s1, s2, bs);
-    case 4: return x_pass_bulk<T, 4>(a, sm, kind, al, upd, he, s1, s2, bs);
-    default: return x_pass_bulk<T, 8>(a, sm, kind, al, upd, he, s1, s2, bs);
+    case 1: x_pass_rows<T, 1>(a, sm, kind, al, upd, he, s1, s2); break;
+    case 2: x_pass_rows<T, 2>(a, sm, kind, al, upd, he, s1, s2); break;
+    case 4: x_pass_rows<T, 4>(a, sm, kind, al, upd, he, s1, s2); break;
+    default: x_pass_rows<T, 8>(a, sm, kind, al, upd, he, s1, s2); break;
   }
 }
 
-// q = A z + beta q, p = z + beta p over the team's cells; the block's shares
+// q = A z + beta q, p = z + beta p over the team's cells; the thread's shares
 // of p.q and, for the prediction of the next residual, r.q and q.q
 template <typename T, bool DFM>
 __device__ void matvec_update(const SArgs<T> &a, const T *z, T beta, bool first, double *sh, double &pq, double &rq,
@@ -860,9 +821,9 @@ __device__ void matvec_update(const SArgs<T> &a, const T *z, T beta, bool first,
       aqq.add(qn * qn);
     }
   }
-  pq = block_sum_n(apq.get(), sh);
-  rq = block_sum_n(arq.get(), sh);
-  qq = block_sum_n(aqq.get(), sh);
+  pq = apq.get();
+  rq = arq.get();
+  qq = aqq.get();
 }
 
 // r -= alpha q, e += alpha p over the team's cells with the sums of r^2 and e
@@ -900,7 +861,7 @@ __device__ void update_cells(const SArgs<T> &a, T al, bool he, CgAcc<T> &sr, CgA
 // Exact residual r = b - A phi with b = -(q - qbar) + sum_d k (E_ext . c_d)
 // (FP64, or double-float words in the FP32 modes: the arithmetic of
 // residual_site in poisson_dev.cuh), two cells per thread with all their
-// loads in flight together; block partials of |r|^2, |b|^2 and sum phi.
+// loads in flight together; the thread's shares of |r|^2, |b|^2 and sum phi.
 template <typename T, bool DFM>
 __device__ void residual_cells(const SArgs<T> &a, double qbar, DF qbar_df, double *sh, double &ar, double &ab,
                                double &ap) {
@@ -991,18 +952,30 @@ __device__ void residual_cells(const SArgs<T> &a, double qbar, DF qbar_df, doubl
       }
     }
   }
-  ar = block_sum_n(sr.get(), sh);
-  ab = block_sum_n(sb.get(), sh);
-  ap = block_sum_n(sp.get(), sh);
+  ar = sr.get();
+  ab = sb.get();
+  ap = sp.get();
+}
+
+// Scalar arithmetic of the iteration (divisions, square roots in FP64) by
+// thread 0 alone, broadcast through shared memory: the FP64 rate of the
+// target is a small fraction of its FP32 rate, and 256 threads repeating a
+// division or a square root cost about a microsecond per phase.  Each call
+// site has its own cell, so a cell is rewritten only after the barriers of
+// the passes in between.
+__device__ __forceinline__ double bcast0(double v, double *cell) {
+  if (threadIdx.x == 0) *cell = v;
+  __syncthreads();
+  return *cell;
 }
 
 template <typename T, bool DFM>
 __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double sh[kSB];
-  __shared__ unsigned long long mbar;
+  __shared__ double bc[8];  // broadcast cells of the scalar arithmetic
+  const bool t0 = threadIdx.x == 0;
   const Smem<T> sm = smem_layout<T>(smem_raw, a);
-  if (threadIdx.x == 0) mbar_init(&mbar);
   load_tables(a, sm);
   const PArgs<T> &pa = a.pa;
   const GridTeam tm{pa.bar, pa.status, pa.spin_limit};
@@ -1013,7 +986,6 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   const int nb = tm.nblocks();
   PDev *st = pa.st;
   const int have_prev = st->have_prev;
-  BulkSync bs{&mbar, 0u, pa.bar, pa.status};
 
   // initial guess 2 phi(t-1) - phi(t-2), sum of q (kU cells per thread in flight)
   SumAcc<DFM> sq;
@@ -1064,11 +1036,12 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
     }
   }
   {
-    const double v = block_sum_n(sq.get(), sh);
-    if (threadIdx.x == 0) pa.part[blockIdx.x] = v;
+    double v[1] = {sq.get()};
+    put_block_sums<1>(v, pa.part, nb, sh);
   }
-  if (!tm.sync()) return;
-  const double qbar = sum_partials(pa.part, nb, sh) / double(N);
+  double qs[1];
+  if (!sync_sums<1>(tm, pa.part, nb, qs, sh)) return;
+  const double qbar = bcast0(t0 ? qs[0] / double(N) : 0.0, &bc[0]);
   const DF qbar_df = df_split(qbar);
 
   const double tol = st->tol;
@@ -1081,22 +1054,18 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
     // exact residual r = b - A phi (FP64 / double-float), |r|^2, |b|^2, sum phi
     double r2, b2, ps;
     {
-      double ar, ab, ap;
-      residual_cells<T, DFM>(a, qbar, qbar_df, sh, ar, ab, ap);
-      if (threadIdx.x == 0) {
-        pa.part[blockIdx.x] = ar;
-        pa.part[nb + blockIdx.x] = ab;
-        pa.part[2 * nb + blockIdx.x] = ap;
-      }
-      if (!tm.sync()) return;
-      r2 = sum_partials(pa.part, nb, sh);
-      b2 = sum_partials(pa.part + nb, nb, sh);
-      ps = sum_partials(pa.part + 2 * nb, nb, sh);
+      double v[3];
+      residual_cells<T, DFM>(a, qbar, qbar_df, sh, v[0], v[1], v[2]);
+      put_block_sums<3>(v, pa.part, nb, sh);
+      if (!sync_sums<3>(tm, pa.part, nb, v, sh)) return;
+      r2 = v[0];
+      b2 = v[1];
+      ps = v[2];
     }
     if (outer == 0) bn = b2;
-    rr = rel_res(r2, bn);
+    rr = bcast0(t0 ? rel_res(r2, bn) : 0.0, &bc[1]);
     exact = true;
-    shift = ps / double(N);
+    shift = bcast0(t0 ? ps / double(N) : 0.0, &bc[2]);
     have_e = false;
     if (rr < tol || it >= max_iter || !isfinite(rr)) break;
     const double rr_start = rr;
@@ -1115,35 +1084,31 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
       const bool upd = !first, he = have_e;
       if (last) {
         update_cells<T>(a, al, he, sr, se);
-      } else if (a.xbulk) {
-        x_pass_bulk_k<T>(a, sm, kXUpdate, al, upd, he, sr, se, bs);
+      } else if (a.xrows) {
+        x_pass_rows_k<T>(a, sm, kXUpdate, al, upd, he, sr, se);
       } else {
         LoadU<T> lu{a.r, a.e, a.q, a.p, al, upd, he, &sr, &se};
         tile_pass<T>(a, sm, 0, kFwd, lu, StoreW<T>{a.w});
       }
       if (upd) have_e = true;
       {
-        const double v0 = block_sum_n(sr.get(), sh);
-        const double v1 = block_sum_n(se.get(), sh);
-        if (threadIdx.x == 0) {
-          pa.part[blockIdx.x] = v0;
-          pa.part[nb + blockIdx.x] = v1;
-        }
+        double v[2] = {sr.get(), se.get()};
+        put_block_sums<2>(v, pa.part, nb, sh);
+        if (!sync_sums<2>(tm, pa.part, nb, v, sh)) return;
+        r2 = v[0];
+        if (have_e) sum_e = v[1];
       }
-      if (!tm.sync()) return;
-      r2 = sum_partials(pa.part, nb, sh);
-      if (have_e) sum_e = sum_partials(pa.part + nb, nb, sh);
       if (upd) {
         ++it;
-        rr = rel_res(r2, bn);
+        rr = bcast0(t0 ? rel_res(r2, bn) : 0.0, &bc[3]);
         exact = false;
         if (rr < target || it >= max_iter || !isfinite(rr)) break;
       }
       if (last) {
         // mispredicted: the x pass of the updated r
-        if (a.xbulk) {
+        if (a.xrows) {
           CgAcc<T> d0, d1;
-          x_pass_bulk_k<T>(a, sm, kXForward, T(0), false, false, d0, d1, bs);
+          x_pass_rows_k<T>(a, sm, kXForward, T(0), false, false, d0, d1);
         } else {
           tile_pass<T>(a, sm, 0, kFwd, LoadW<T>{a.r}, StoreW<T>{a.w});
         }
@@ -1158,41 +1123,37 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
       tile_pass<T>(a, sm, 1, kInv, lw, StoreW<T>{a.w});
       if (!tm.sync()) return;
       CgAcc<T> srz;
-      if (a.xbulk) {
+      if (a.xrows) {
         CgAcc<T> d1;
-        x_pass_bulk_k<T>(a, sm, kXInverse, T(0), false, false, srz, d1, bs);
+        x_pass_rows_k<T>(a, sm, kXInverse, T(0), false, false, srz, d1);
       } else {
         tile_pass<T>(a, sm, 0, kInv, LoadWR<T>{a.w, a.r}, StoreRZ<T>{a.w, a.r, &srz});
       }
       {
-        const double v = block_sum_n(srz.get(), sh);
-        if (threadIdx.x == 0) pa.part[blockIdx.x] = v;
+        double v[1] = {srz.get()};
+        put_block_sums<1>(v, pa.part, nb, sh);
       }
-      if (!tm.sync()) return;
-      const double rho = sum_partials(pa.part, nb, sh);
-      const double beta = first ? 0.0 : rho / rho_old;
+      double rz[1];
+      if (!sync_sums<1>(tm, pa.part, nb, rz, sh)) return;
+      const double rho = rz[0];
+      const double beta = bcast0(t0 && !first ? rho / rho_old : 0.0, &bc[4]);
       // F: search direction and its image
       {
-        double v0, v1, v2;
-        matvec_update<T, DFM>(a, a.w, T(beta), first, sh, v0, v1, v2);
-        if (threadIdx.x == 0) {
-          pa.part[blockIdx.x] = v0;
-          pa.part[nb + blockIdx.x] = v1;
-          pa.part[2 * nb + blockIdx.x] = v2;
-        }
+        double v[3];
+        matvec_update<T, DFM>(a, a.w, T(beta), first, sh, v[0], v[1], v[2]);
+        put_block_sums<3>(v, pa.part, nb, sh);
       }
-      if (!tm.sync()) return;
-      const double pq = sum_partials(pa.part, nb, sh);
-      const double rq = sum_partials(pa.part + nb, nb, sh);
-      const double qq = sum_partials(pa.part + 2 * nb, nb, sh);
-      alpha = pq != 0.0 ? rho / pq : 0.0;
+      double fs[3];
+      if (!sync_sums<3>(tm, pa.part, nb, fs, sh)) return;
+      const double pq = fs[0], rq = fs[1], qq = fs[2];
+      alpha = bcast0(t0 && pq != 0.0 ? rho / pq : 0.0, &bc[5]);
       rho_old = rho;
       first = false;
       // |r - alpha q|^2 from the sums (the same in every block)
-      const double r2n = r2 - 2.0 * alpha * rq + alpha * alpha * qq;
-      last = it + 1 >= max_iter || rel_res(fmax(r2n, 0.0), bn) < target;
+      last = it + 1 >= max_iter ||
+             bcast0(t0 ? rel_res(fmax(r2 - 2.0 * alpha * rq + alpha * alpha * qq, 0.0), bn) : 0.0, &bc[6]) < target;
     }
-    shift += sum_e / double(N);
+    shift += bcast0(t0 ? sum_e / double(N) : 0.0, &bc[7]);
     if (it >= max_iter || !isfinite(rr) || (carry && rr + kEstErr * rr_start < tol)) break;
     // apply the correction and check it with an exact residual
     for (long long i = gt; i < N; i += G) {
@@ -1297,9 +1258,19 @@ template <typename T> static bool spectral_setup(Spectral *s, const Dims &d) {
     s->allocs.push_back(ptr);
     return ptr;
   };
+  // the five work arrays in one allocation, each start skewed by an odd
+  // number of 256-byte lines from the power-of-two strides of the lattice, so
+  // that the same site of the five arrays (read and written together by the
+  // passes) does not fall into the same L2 sets
   const size_t nb = sizeof(T) * (size_t)d.N;
-  if (!(s->r = dal(nb)) || !(s->p = dal(nb)) || !(s->q = dal(nb)) || !(s->e = dal(nb)) || !(s->w = dal(nb)))
-    return false;
+  const size_t stride = ((nb + 255) & ~size_t(255)) + 97 * 256;
+  unsigned char *base = (unsigned char *)dal(5 * stride);
+  if (!base) return false;
+  s->r = base;
+  s->p = base + stride;
+  s->q = base + 2 * stride;
+  s->e = base + 3 * stride;
+  s->w = base + 4 * stride;
   const int ns[3] = {d.nx, d.ny, d.nz};
   size_t tiles = 0;
   for (int A = 0; A < 3; ++A) {
@@ -1418,8 +1389,8 @@ template <typename T, bool DFM> static int launch(Spectral *s, const Ctx &c, con
   a.e = (T *)s->e;
   a.w = (T *)s->w;
   a.inv_eref_n = T(1.0 / (s->eps_ref * double(c.d.N)));
-  // rows of nx words start on 16-byte boundaries (cudaMalloc'd arrays)
-  a.xbulk = reg_fft_k(c.d.nx) != 0 && (c.d.nx * sizeof(T)) % 16 == 0;
+  // rows of nx words start on 16-byte boundaries (arrays 256-byte aligned)
+  a.xrows = reg_fft_k(c.d.nx) != 0 && (c.d.nx * sizeof(T)) % 16 == 0;
   if (cudaMemsetAsync(pa.bar, 0, sizeof(Bar), st) != cudaSuccess) return -1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(s->grid);
