@@ -17,9 +17,10 @@
 //   Y  pass along y;        X  pass along x (w = z = M^-1 r; sum r.z);
 //   F  p = z + beta p, q = A z + beta q (sums p.q, r.q, q.q).
 // The sums of F give |r - alpha q|^2 before the update is made: when it is
-// predicted below the target the next U is the update alone (the x pass of
-// the last iteration would be discarded), and a wrong prediction runs the x
-// pass as a phase of its own.
+// predicted below the target the next U is the update alone with its own
+// sums (the x pass of the last iteration would be discarded), and a wrong
+// prediction runs the x pass as a phase of its own.  Otherwise the sums of U
+// (|r|^2, e) are reduced together with r.z after the X pass.
 // Between the forward and the inverse pass along an axis whose lines are
 // transformed in registers, the work array holds that axis's frequencies in
 // the transform's own storage order; the symbols are stored in that order.
@@ -77,22 +78,49 @@ template <typename T> struct CgAcc {
 
 __device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+// c / x for the symbol scaling of the register passes: the preconditioner
+// only has to be the same symmetric positive operator at every application,
+// so FP32 takes the fast division intrinsic (about 2 ulp; x in (0, 12])
+__device__ __forceinline__ float sym_div(float c, float x) { return __fdividef(c, x); }
+__device__ __forceinline__ double sym_div(double c, double x) { return c / x; }
 
+// Fixed-order sums of M values at once: a shared-memory tree over the block
+// whose levels add all M values (the FP64 additions of M separate trees, but
+// one set of barriers); only the active threads of a level add (the FP64 rate
+// of the target is low).  sh holds M kSB doubles.
+template <int M> __device__ __forceinline__ void block_sum_m(double (&v)[M], double *sh) {
+#pragma unroll
+  for (int m = 0; m < M; ++m) sh[m * kSB + threadIdx.x] = v[m];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int m = 0; m < M; ++m) sh[m * kSB + threadIdx.x] += sh[m * kSB + threadIdx.x + w];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) v[m] = sh[m * kSB];
+  __syncthreads();
+}
 // The blocks' sums of M per-thread values into part[m nb + blockIdx.x], and
 // after the grid barrier the M grid sums, added by every block in the same
 // fixed order (every block holds bitwise the same scalars and takes the same
-// branches).  One value at a time: measured faster than reducing M values
-// together at 128^3.
+// branches).
 template <int M> __device__ __forceinline__ void put_block_sums(double (&v)[M], double *part, int nb, double *sh) {
-  for (int m = 0; m < M; ++m) {
-    const double t = block_sum_n(v[m], sh);
-    if (threadIdx.x == 0) part[m * nb + blockIdx.x] = t;
-  }
+  block_sum_m<M>(v, sh);
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int m = 0; m < M; ++m) part[m * nb + blockIdx.x] = v[m];
 }
 template <int M>
 __device__ __forceinline__ bool sync_sums(const GridTeam &tm, double *part, int nb, double (&v)[M], double *sh) {
   if (!tm.sync()) return false;
-  for (int m = 0; m < M; ++m) v[m] = sum_partials(part + m * nb, nb, sh);
+#pragma unroll
+  for (int m = 0; m < M; ++m) v[m] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int m = 0; m < M; ++m) v[m] += part[m * nb + b];
+  block_sum_m<M>(v, sh);
   return true;
 }
 
@@ -285,8 +313,8 @@ __device__ __forceinline__ void reg_line_pair(C2<T> *X, int mode, const C2<T> *l
       for (int k = 0; k < K; ++k) {
         const int s = lane + 32 * k;
         const T z = sc.sz[s];
-        const T ca = sc.va && (sc.nza || s != 0) ? sc.c * recip(sc.sa0 + z) : T(0);
-        const T cb = sc.vb ? sc.c * recip(sc.sb0 + z) : T(0);
+        const T ca = sc.va && (sc.nza || s != 0) ? sym_div(sc.c, sc.sa0 + z) : T(0);
+        const T cb = sc.vb ? sym_div(sc.c, sc.sb0 + z) : T(0);
         v[k] = C2<T>{ha[k] * ca, hb[k] * cb};
       }
       dit_regs<T, K>(v, lt, lane);
@@ -972,7 +1000,7 @@ __device__ __forceinline__ double bcast0(double v, double *cell) {
 template <typename T, bool DFM>
 __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double sh[kSB];
+  __shared__ double sh[3 * kSB];  // block sums of up to three values
   __shared__ double bc[8];  // broadcast cells of the scalar arithmetic
   const bool t0 = threadIdx.x == 0;
   const Smem<T> sm = smem_layout<T>(smem_raw, a);
@@ -1077,34 +1105,24 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
     bool first = true;
     bool last = false;  // the coming update is predicted to end the iteration
     for (;;) {
-      // U: update r and e, Hartley pass along x of r into w (the update alone
-      // when it is predicted to be the last)
+      // U: update r and e, Hartley pass along x of r into w.  Its sums of
+      // |r|^2 and e join the reduction of r.z one phase later; only the
+      // update predicted to be the last runs alone with its own reduction.
       CgAcc<T> sr, se;
       const T al = T(alpha);
       const bool upd = !first, he = have_e;
       if (last) {
         update_cells<T>(a, al, he, sr, se);
-      } else if (a.xrows) {
-        x_pass_rows_k<T>(a, sm, kXUpdate, al, upd, he, sr, se);
-      } else {
-        LoadU<T> lu{a.r, a.e, a.q, a.p, al, upd, he, &sr, &se};
-        tile_pass<T>(a, sm, 0, kFwd, lu, StoreW<T>{a.w});
-      }
-      if (upd) have_e = true;
-      {
+        have_e = true;
         double v[2] = {sr.get(), se.get()};
         put_block_sums<2>(v, pa.part, nb, sh);
         if (!sync_sums<2>(tm, pa.part, nb, v, sh)) return;
         r2 = v[0];
-        if (have_e) sum_e = v[1];
-      }
-      if (upd) {
+        sum_e = v[1];
         ++it;
         rr = bcast0(t0 ? rel_res(r2, bn) : 0.0, &bc[3]);
         exact = false;
         if (rr < target || it >= max_iter || !isfinite(rr)) break;
-      }
-      if (last) {
         // mispredicted: the x pass of the updated r
         if (a.xrows) {
           CgAcc<T> d0, d1;
@@ -1112,8 +1130,19 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
         } else {
           tile_pass<T>(a, sm, 0, kFwd, LoadW<T>{a.r}, StoreW<T>{a.w});
         }
-        if (!tm.sync()) return;
+      } else {
+        if (a.xrows) {
+          x_pass_rows_k<T>(a, sm, kXUpdate, al, upd, he, sr, se);
+        } else {
+          LoadU<T> lu{a.r, a.e, a.q, a.p, al, upd, he, &sr, &se};
+          tile_pass<T>(a, sm, 0, kFwd, lu, StoreW<T>{a.w});
+        }
+        if (upd) {
+          have_e = true;
+          ++it;
+        }
       }
+      if (!tm.sync()) return;
       // preconditioner: Y, Z (scale), Y, X passes on w
       const LoadW<T> lw{a.w};
       tile_pass<T>(a, sm, 1, kFwd, lw, StoreW<T>{a.w});
@@ -1129,13 +1158,19 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
       } else {
         tile_pass<T>(a, sm, 0, kInv, LoadWR<T>{a.w, a.r}, StoreRZ<T>{a.w, a.r, &srz});
       }
-      {
-        double v[1] = {srz.get()};
-        put_block_sums<1>(v, pa.part, nb, sh);
-      }
-      double rz[1];
-      if (!sync_sums<1>(tm, pa.part, nb, rz, sh)) return;
+      double rz[3] = {srz.get(), sr.get(), se.get()};
+      put_block_sums<3>(rz, pa.part, nb, sh);
+      if (!sync_sums<3>(tm, pa.part, nb, rz, sh)) return;
       const double rho = rz[0];
+      if (upd) {
+        // the residual and the correction after this iteration's update: a
+        // convergence the prediction missed ends the iteration here
+        r2 = rz[1];
+        sum_e = rz[2];
+        rr = bcast0(t0 ? rel_res(r2, bn) : 0.0, &bc[3]);
+        exact = false;
+        if (rr < target || it >= max_iter || !isfinite(rr)) break;
+      }
       const double beta = bcast0(t0 && !first ? rho / rho_old : 0.0, &bc[4]);
       // F: search direction and its image
       {
