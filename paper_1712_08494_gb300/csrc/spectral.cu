@@ -1207,7 +1207,41 @@ __global__ void __launch_bounds__(kSB, 2) k_spectral(SArgs<T> a) {
   // phi += e (when pending), mean-free
   const bool zero = bn == 0.0;
   const DF shift_df = df_split(shift);
-  for (long long i0 = gt; i0 < N; i0 += kU * G) {
+  // FP32 modes, N a multiple of 4: four cells per 16-byte access (the
+  // arrays start 256-byte aligned), two groups in flight per thread
+  const long long N4 = DFM && (N & 3) == 0 ? N / 4 : 0;
+  if constexpr (DFM) {
+    for (long long j0 = gt; j0 < N4; j0 += 2 * G) {
+      float4 h[2], l[2], ev[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const long long j = j0 + u * G;
+        const bool in = j < N4 && !zero;
+        const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+        h[u] = in ? reinterpret_cast<const float4 *>(pa.phi_hi)[j] : z4;
+        l[u] = in ? reinterpret_cast<const float4 *>(pa.phi_lo)[j] : z4;
+        ev[u] = in && have_e ? reinterpret_cast<const float4 *>(a.e)[j] : z4;
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const long long j = j0 + u * G;
+        if (j >= N4) continue;
+        const float hh[4] = {h[u].x, h[u].y, h[u].z, h[u].w}, ll[4] = {l[u].x, l[u].y, l[u].z, l[u].w};
+        const float ee[4] = {ev[u].x, ev[u].y, ev[u].z, ev[u].w};
+        float oh[4], ol[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          DF v{0.f, 0.f};
+          if (!zero) v = df_sub(df_add(DF{hh[c], ll[c]}, DF{ee[c], 0.f}), shift_df);
+          oh[c] = v.hi;
+          ol[c] = v.lo;
+        }
+        reinterpret_cast<float4 *>(pa.phi_hi)[j] = make_float4(oh[0], oh[1], oh[2], oh[3]);
+        reinterpret_cast<float4 *>(pa.phi_lo)[j] = make_float4(ol[0], ol[1], ol[2], ol[3]);
+      }
+    }
+  }
+  for (long long i0 = gt + 4 * N4; i0 < N; i0 += kU * G) {
     if constexpr (DFM) {
       float h[kU], l[kU], ev[kU];
 #pragma unroll
