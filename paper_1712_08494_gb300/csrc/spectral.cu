@@ -357,6 +357,8 @@ template <typename T> __device__ __forceinline__ void cp_pair(C2<T> *dst, const 
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_newest_pending() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 // line pair (a at ia, b at ib or missing) of array p into packed slot d
 template <typename T>
 __device__ __forceinline__ void cp_line_pair(C2<T> *d, const T *p, unsigned ia, unsigned ib, bool hb, bool adj) {
@@ -385,6 +387,7 @@ template <typename T> struct Bufs {
 // aux slots (register transforms only: the plan stages use bB).
 template <typename T> struct LoadW {
   static constexpr bool kFinish = false;
+  static constexpr bool kDouble = true;  // no aux slots: tiles can be double-buffered
   const T *w;
   __device__ __forceinline__ void stage(unsigned ia, unsigned ib, bool hb, bool adj, const Bufs<T> &b, int s) const {
     cp_line_pair(b.A + s, w, ia, ib, hb, adj);
@@ -394,6 +397,7 @@ template <typename T> struct LoadW {
 // stages w and keeps r in the aux slot (the last x pass: r.z at the store)
 template <typename T> struct LoadWR {
   static constexpr bool kFinish = false;
+  static constexpr bool kDouble = false;
   const T *w, *r;
   __device__ __forceinline__ void stage(unsigned ia, unsigned ib, bool hb, bool adj, const Bufs<T> &b, int s) const {
     cp_line_pair(b.A + s, w, ia, ib, hb, adj);
@@ -404,6 +408,7 @@ template <typename T> struct LoadWR {
 // r -= alpha q and e += alpha p (upd), sums of r^2 and e; stages r
 template <typename T> struct LoadU {
   static constexpr bool kFinish = true;
+  static constexpr bool kDouble = false;
   T *r, *e;
   const T *q, *p;
   T al;
@@ -505,6 +510,73 @@ __device__ void tile_pass(const SArgs<T> &a, const Smem<T> &sm, int A, int mode,
   // y and z passes: the thread's pair, its first position and position step
   const int myp = threadIdx.x & (pairs - 1), myq = threadIdx.x >> lgP, qstep = B >> lgP;
   const unsigned step = A == 1 ? sy : sz;
+  if constexpr (Load::kDouble) {
+    if (regK && A != 0) {
+      // y and z passes with register transforms: tile t + grid is copied into
+      // the other buffer while tile t is transformed and stored
+      C2<T> *const slot0 = bA, *const slot1 = bB + pairs * ld;
+      const bool adj = (g.nx & 1) == 0;  // even rows: every pair (x, x + 1) is aligned
+      auto stage = [&](int t, C2<T> *buf) {
+        const int o = t / xt, x = ((t - o * xt) << lgW) + 2 * myp;
+        const bool va = x < g.nx, vb = x + 1 < g.nx;
+        const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x);
+        const Bufs<T> bf{buf, nullptr, nullptr, nullptr, nullptr};
+        for (int pos = myq; pos < N; pos += qstep) {
+          const unsigned i = base + unsigned(pos) * step;
+          if (va) ldr.stage(i, i + 1u, vb, adj, bf, myp * ld + pos);
+          else buf[myp * ld + pos] = C2<T>{T(0), T(0)};
+        }
+      };
+      if (int(blockIdx.x) < nt) stage(blockIdx.x, slot0);
+      cp_commit();
+      int k = 0;
+      for (int t = blockIdx.x; t < nt; t += gridDim.x, ++k) {
+        const int tn = t + gridDim.x;
+        if (tn < nt) stage(tn, (k & 1) ? slot0 : slot1);
+        cp_commit();
+        cp_wait_newest_pending();  // tile t has landed
+        __syncthreads();
+        C2<T> *cur = (k & 1) ? slot1 : slot0;
+        const int o = t / xt, x0 = (t - o * xt) << lgW;
+        const C2<T> *lt = sm.lanetw + (A * 32 + lane) * kLaneTw;
+        ScaleZ<T> sc{};
+        const T *sx = sm.sym + a.ax[0].s_at, *sy_ = sm.sym + a.ax[1].s_at;
+        sc.sz = sm.sym + a.ax[2].s_at;
+        sc.c = -a.inv_eref_n;
+        for (int mi = 0; mi < nm; ++mi) {
+          const int m = warp + mi * nw;
+          if (mode == kFused) {
+            const int kxa = x0 + 2 * m, kxb = kxa + 1, ky = o;
+            sc.va = kxa < g.nx;
+            sc.vb = kxb < g.nx;
+            sc.sa0 = sc.va ? sx[kxa] + sy_[ky] : T(1);
+            sc.sb0 = sc.vb ? sx[kxb] + sy_[ky] : T(1);
+            sc.nza = (kxa | ky) != 0;
+          }
+          C2<T> *line = cur + m * ld;
+          switch (regK) {
+            case 1: reg_line_pair<T, 1>(line, mode, lt, lane, sc); break;
+            case 2: reg_line_pair<T, 2>(line, mode, lt, lane, sc); break;
+            case 4: reg_line_pair<T, 4>(line, mode, lt, lane, sc); break;
+            default: reg_line_pair<T, 8>(line, mode, lt, lane, sc); break;
+          }
+        }
+        __syncthreads();
+        const int x = x0 + 2 * myp;
+        if (x < g.nx) {
+          const unsigned base = (A == 1 ? unsigned(o) * sz : unsigned(o) * sy) + unsigned(x);
+          const bool vb = x + 1 < g.nx;
+          for (int pos = myq; pos < N; pos += qstep) {
+            const unsigned i = base + unsigned(pos) * step;
+            store(i, i + 1u, vb, adj, cur[myp * ld + pos], nullptr);
+          }
+        }
+        __syncthreads();  // the buffer is staged again two tiles on
+      }
+      cp_wait_all();
+      return;
+    }
+  }
   for (int t = blockIdx.x; t < nt; t += gridDim.x) {
     // tile origin: first row (x pass) or (x0, o) with o = z (y pass) or y (z pass)
     const int o = A == 0 ? 0 : t / xt;
