@@ -336,6 +336,7 @@ def run_ours(args):
     sampler = None
     for prec in ("fp32", "bf16", "fp16"):
         w = synth.droplet(n=n, r=24.0 * n / 128.0, prec=prec, seed=1 + rank)
+        w.params.poisson_solver = args.solver
         sysg = lbeh.System(w.params, stream.cuda_stream)
         sysg.set_fields(rho=list(w.rho), n=list(w.n))
         if args.relax:
@@ -388,6 +389,7 @@ def run_ours(args):
     # end-to-end through the C-ABI with pinned host buffers: every step loads
     # the state from host memory, advances one step and reads the observables back
     w = synth.droplet(n=n, r=24.0 * n / 128.0, prec="fp32", seed=1 + rank)
+    w.params.poisson_solver = args.solver
     host = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).pin_memory()
             for a in (w.rho[0], w.rho[1], w.n[0], w.n[1])]
     sysg = lbeh.System(w.params, stream.cuda_stream)
@@ -649,6 +651,8 @@ def main():
     ap.add_argument("--size", type=int, default=SIZE)
     ap.add_argument("--relax", type=int, default=200,
                     help="untimed steps before the warm-up that take the droplet past its start-up transient")
+    ap.add_argument("--solver", default="auto", choices=["auto", "spectral", "multigrid"],
+                    help="Poisson solver of the droplet runs (auto: spectral for the droplet)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the suspension, batch and adjoint measurements")

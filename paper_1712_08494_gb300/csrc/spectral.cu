@@ -130,7 +130,8 @@ __device__ __forceinline__ bool sync_sums(const GridTeam &tm, double *part, int 
 // one warp (dif_regs, dit_regs below); its per-lane twiddles live in shared
 // memory: kLaneTw slots per lane and axis, K - 1 of W_N^(lane kappa), the five
 // cross-lane twiddles of the decimation-in-frequency stages, then the five of
-// the decimation-in-time stages (1 on the stage's top lanes).
+// the decimation-in-time stages (both 1 on a stage's top lanes, so a stage is
+// two FMAs and one complex product on every lane, no select).
 constexpr int kLaneTw = 17;
 __host__ __device__ inline int reg_fft_k(int N) {
   return (N == 32 || N == 64 || N == 128 || N == 256) ? N / 32 : 0;
@@ -181,7 +182,7 @@ template <typename T> __device__ void load_tables(const SArgs<T> &a, const Smem<
       for (int kap = 1; kap < K; ++kap) lt[kap - 1] = root<T>(lane * kap, X.P.n);
       for (int st = 0; st < 5; ++st) {
         const int h = 16 >> st;
-        lt[7 + st] = root<T>((lane & (h - 1)) * (16 / h), 32);
+        lt[7 + st] = (lane & h) ? root<T>((lane & (h - 1)) * (16 / h), 32) : C2<T>{T(1), T(0)};
         const int h2 = 1 << st;
         lt[12 + st] = (lane & h2) ? root<T>((lane & (h2 - 1)) * (16 / h2), 32) : C2<T>{T(1), T(0)};
       }
@@ -211,14 +212,14 @@ __device__ __forceinline__ void dif_regs(C2<T> (&v)[K], const C2<T> *lt, int lan
 #pragma unroll
   for (int st = 0; st < 5; ++st) {
     const int h = 16 >> st;
-    const bool bottom = (lane & h) != 0;
-    const C2<T> w = lt[7 + st];
+    const T sg = (lane & h) ? T(-1) : T(1);  // bottom lanes take partner - own
+    const C2<T> w = lt[7 + st];               // W_2h^(l mod h) on bottom lanes, 1 on top lanes
 #pragma unroll
     for (int kap = 0; kap < K; ++kap) {
       C2<T> u;
       u.x = __shfl_xor_sync(0xffffffffu, v[kap].x, h);
       u.y = __shfl_xor_sync(0xffffffffu, v[kap].y, h);
-      v[kap] = bottom ? cmul(csub(u, v[kap]), w) : cadd(v[kap], u);
+      v[kap] = cmul(C2<T>{fma(sg, v[kap].x, u.x), fma(sg, v[kap].y, u.y)}, w);
     }
   }
 }
@@ -227,15 +228,15 @@ __device__ __forceinline__ void dit_regs(C2<T> (&v)[K], const C2<T> *lt, int lan
 #pragma unroll
   for (int st = 0; st < 5; ++st) {
     const int h = 1 << st;
-    const bool bottom = (lane & h) != 0;
-    const C2<T> w = lt[12 + st];  // W_2h^(l mod h) on bottom lanes, 1 on top lanes
+    const T sg = (lane & h) ? T(-1) : T(1);  // top: own + partner's product, bottom: partner - own product
+    const C2<T> w = lt[12 + st];              // W_2h^(l mod h) on bottom lanes, 1 on top lanes
 #pragma unroll
     for (int kap = 0; kap < K; ++kap) {
       const C2<T> s = cmul(v[kap], w);
       C2<T> r;
       r.x = __shfl_xor_sync(0xffffffffu, s.x, h);
       r.y = __shfl_xor_sync(0xffffffffu, s.y, h);
-      v[kap] = bottom ? csub(r, s) : cadd(v[kap], r);
+      v[kap] = C2<T>{fma(sg, s.x, r.x), fma(sg, s.y, r.y)};
     }
   }
 #pragma unroll
