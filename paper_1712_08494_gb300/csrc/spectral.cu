@@ -971,7 +971,12 @@ __device__ void residual_cells(const SArgs<T> &a, double qbar, DF qbar_df, doubl
   const Dims d = L0.dims();
   const long long G = (long long)gridDim.x * blockDim.x;
   constexpr int U = 2;
-  SumAcc<DFM> sr, sb, sp;
+  // per-thread sums of a few dozen cells: FP32 in the FP32 modes (relative
+  // error ~1e-6 of |r|^2 and |b|^2, far inside the margins of the tests they
+  // steer; the sum of phi only sets the mean shift, ~1e-10 of phi per site),
+  // FP64 in the FP64 mode
+  using Acc = typename std::conditional<DFM, CgAcc<float>, SumAcc<false>>::type;
+  Acc sr, sb, sp;
   Walk wk(blockIdx.x * (long long)blockDim.x + threadIdx.x, G, d.nx, d.ny);
   while (wk.z < d.nz) {
     Nbr c[U];

@@ -473,12 +473,16 @@ __device__ __forceinline__ void np_site(const StepK<T> &k, const T *__restrict__
     nn[N + i] = T(0);
     return;
   }
-  int x, y, z;
-  coords(d, i, x, y, z);
-  const long long jm[3] = {site(d, wrapm(x, d.nx), y, z), site(d, x, wrapm(y, d.ny), z),
-                           site(d, x, y, wrapm(z, d.nz))};
-  const long long jp[3] = {site(d, wrapp(x, d.nx), y, z), site(d, x, wrapp(y, d.ny), z),
-                           site(d, x, y, wrapp(z, d.nz))};
+  // 32-bit site arithmetic (boxes below 2^31 sites): one unsigned division per
+  // axis instead of the 64-bit ones, neighbours by periodic offsets
+  const unsigned ii = unsigned(i), unx = unsigned(d.nx), uny = unsigned(d.ny);
+  const unsigned r = ii / unx, x = ii - r * unx;
+  const unsigned z = r / uny, y = r - z * uny;
+  const unsigned nxy = unx * uny;
+  const unsigned jm[3] = {x == 0 ? ii + unx - 1u : ii - 1u, y == 0 ? ii + (uny - 1u) * unx : ii - unx,
+                          z == 0 ? ii + (unsigned(d.nz) - 1u) * nxy : ii - nxy};
+  const unsigned jp[3] = {x + 1u == unx ? ii + 1u - unx : ii + 1u, y + 1u == uny ? ii - (uny - 1u) * unx : ii + unx,
+                          z + 1u == unsigned(d.nz) ? ii - (unsigned(d.nz) - 1u) * nxy : ii + nxy};
   bool okp[3], okm[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
