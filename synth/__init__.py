@@ -279,6 +279,38 @@ def interface_colloid(n=64, r=8.0, dz=0.0, salt=0.0, dmu=(4.0, 4.0), q=0.0, G=4.
                     note="sphere r=%g at a flat interface, dz=%g, salt=%g" % (r, dz, salt))
 
 
+def coated_droplet(n=128, rd=32.0, ncoll=80, rp=5.0, seed=5, prec="fp32", salt=1e-3, dmu=(4.0, -4.0), Ez=1e-3,
+                   G=4.0, tol=1e-6, steps=2000) -> Workload:
+    """Colloid-coated droplet (Sec. III.G): a drop of radius rd (fluid b) at
+    the box centre, as the charged drop of Sec. III.D (uniform salt, Gibbs
+    transfer energies dmu, equal fluid permittivities, field along z), with ncoll
+    uncharged moving spheres of radius rp centred on the drop surface at the
+    points of a Fibonacci lattice on the sphere (a homogeneous coating:
+    covering fraction ncoll rp^2 / (4 rd^2)), particle permittivity 10/80 of
+    the fluids', neutral wetting (interface solid nodes take the mean density
+    of their fluid neighbours)."""
+    rng = np.random.default_rng(seed)
+    shape = (n, n, n)
+    x, y, z = _grid(n, n, n)
+    c = n / 2.0
+    inside = (x - c) ** 2 + (y - c) ** 2 + (z - c) ** 2 < rd * rd
+    red = np.where(inside, 0.04, 0.7) * _noise(rng, shape, 0.01)
+    blue = np.where(inside, 0.7, 0.04) * _noise(rng, shape, 0.01)
+    rho = np.stack([red, blue])
+    k = np.arange(ncoll) + 0.5
+    polar = np.arccos(1.0 - 2.0 * k / ncoll)
+    azim = math.pi * (1.0 + math.sqrt(5.0)) * k
+    cx = c + rd * np.stack([np.cos(azim) * np.sin(polar), np.sin(azim) * np.sin(polar), np.cos(polar)], axis=1)
+    cr = np.full(ncoll, float(rp))
+    ions = np.full((2,) + shape, float(salt))  # uniform: the transfer energies charge the drop over time
+    p = Params(nx=n, ny=n, nz=n, ncomp=2, nions=2, prec=prec, tau=1.0, G=G, D=0.05, bjerrum=0.4,
+               eps_r=(1.0, 1.0), eps_r_colloid=0.125, dmu=tuple(float(v) for v in dmu), drho_a=0.66,
+               E_ext=(0.0, 0.0, Ez), poisson_tol=tol, poisson_max_iter=50, ncolloid_max=ncoll, colloids_move=1,
+               rho0_shift=(0.04, 0.04))
+    return Workload("coated_droplet_%d" % n, p, rho, ions, cx, np.zeros_like(cx), np.zeros(ncoll), cr, steps,
+                    "drop r=%g coated by %d spheres r=%g, E_z=%g" % (rd, ncoll, rp, Ez))
+
+
 def shear_wave(n=32, U=1e-3, rho=1.0, tau=1.0) -> Workload:
     """Single-component, ion-free periodic box whose initial velocity is the
     shear wave u_x(z) = U sin(2 pi z / n) (density uniform)."""

@@ -46,3 +46,20 @@ def test_flat_interface_recipe():
     ea, eb = w.params.eps_r
     assert abs((ea - eb) / (ea + eb) - chi) < 1e-15
     assert tuple(w.params.dmu) == dmu
+
+
+def test_coated_droplet_recipe():
+    """Sec. III.G: 80 spheres of radius 5 on the surface of a drop of radius
+    32 (covering fraction N rp^2 / (4 rd^2) = 0.49, the paper's ~0.48), no
+    two overlapping, uncharged, particle permittivity 10/80 of the fluids'."""
+    w = synth.coated_droplet(n=128)
+    c = 64.0
+    r = np.sqrt(((w.colloid_x - c) ** 2).sum(axis=1))
+    assert w.colloid_x.shape == (80, 3) and np.allclose(r, 32.0)
+    d = np.sqrt(((w.colloid_x[:, None, :] - w.colloid_x[None, :, :]) ** 2).sum(-1))
+    np.fill_diagonal(d, np.inf)
+    assert d.min() > 2 * 5.0
+    assert abs(80 * 25.0 / (4 * 32.0 ** 2) - 0.488) < 1e-3
+    assert np.all(w.colloid_q == 0.0) and w.params.eps_r_colloid == 0.125
+    assert w.params.ncolloid_max == 80 and w.params.colloids_move == 1
+    assert abs(float(w.n[0].sum() - w.n[1].sum())) < 1e-9  # neutral start
