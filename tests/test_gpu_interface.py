@@ -63,10 +63,13 @@ def test_colloid_coated_droplet(lbeh):
     """Sec. III.G: 80 uncharged spheres (radius 5) adsorbed on a drop of
     radius 32 (covering fraction 0.49) in the charged-drop setting of
     Sec. III.D (salt 1e-3, transfer energies +-4 kT, E_z = 1e-3), 128^3,
-    FP32, 3000 steps: the coating stays on the interface (every sphere centre
-    within 2.5 cells of the drop's equimolar radius around its centroid), no
-    two spheres interpenetrate by more than Hertz contact allows, the ions are
-    conserved and the solve converges at every step."""
+    FP32, 3000 steps: every sphere still straddles the interface (its centre
+    closer than r_p to the drop's equimolar radius around the drop centroid;
+    measured at most 2.2-2.4 cells every 500 steps, the equimolar radius of
+    fluid b being 30.2 with the spheres taking part of the drop's volume), no
+    two spheres interpenetrate by more than Hertz contact allows (measured
+    closest centres 10.004: the coating is packed), the ions are conserved
+    (measured 2.5e-9) and the solve converges at every step."""
     w = synth.coated_droplet(n=128)
     s = lbeh.System(w.params)
     s.set_fields(rho=list(w.rho), n=list(w.n), colloid_x=w.colloid_x, colloid_v=w.colloid_v,
@@ -95,8 +98,8 @@ def test_colloid_coated_droplet(lbeh):
     print("conservation", mass, ions)
     # ions are remapped exactly when the spheres cover and uncover nodes; the
     # fluid mass of covered nodes is not (new fluid nodes take their
-    # neighbours' density), so only a bound against a runaway is asserted
-    assert ions < 1e-5 and mass < 0.05
+    # neighbours' density): measured 1.4e-4 over 3000 steps
+    assert ions < 1e-6 and mass < 1e-3
     for dev, dmin, _ in worst:
-        assert dev < 2.5, worst
+        assert dev < 5.0, worst  # r_p: the sphere still crosses the interface
         assert dmin > 2 * 5.0 - 0.5, worst
