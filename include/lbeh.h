@@ -49,7 +49,9 @@ extern "C" {
 /* Arithmetic and storage of the populations.  FP64: all FP64.  FP32: FP32
  * compute and storage.  *_BF16STORE / *_FP16STORE: FP32 compute, populations
  * stored as f - w_q rho0_shift[sigma] in bf16 / fp16.  The potential is held
- * in FP64 in every mode (FP32 multigrid corrections with FP64 residuals). */
+ * in FP64 (FP64 mode) or as a double-float pair of FP32 words (FP32 modes),
+ * the Poisson residuals formed in that precision and the corrections in the
+ * compute type. */
 typedef enum {
   LBEH_FP64 = 0,
   LBEH_FP32 = 1,
@@ -165,7 +167,10 @@ int lbeh_get_fields(lbeh_handle *h, lbeh_fields *out);
 int lbeh_step(lbeh_handle *h, int nsteps);
 
 /* Conserved sums, drop deformation and colloid drift, reduced on the device
- * in FP64 in a fixed order (bitwise reproducible).  Synchronises. */
+ * in a fixed order (bitwise reproducible): per-site values in the compute
+ * type, per-thread running sums in double-float words (FP32 modes, products
+ * of the drop moments formed exactly) or FP64, block and grid sums in FP64.
+ * Synchronises. */
 int lbeh_observables(lbeh_handle *h, lbeh_obs *out);
 
 /* Auxiliary read-outs for validation (host destination, FP64 unless noted):

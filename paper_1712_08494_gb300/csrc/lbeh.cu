@@ -27,6 +27,14 @@ struct lbeh_handle {
   double last_relres = 0.0;
   bool loaded = false;
   std::vector<double> hx, hv, hq, hr, hf;  // host copy of the colloid table
+  // staging buffers of set/get calls, kept between calls (device memory is
+  // not allocated and freed per call; a cudaFree synchronises the device)
+  struct Stage {
+    void *p;
+    size_t bytes;
+    bool busy;
+  };
+  std::vector<Stage> stage;
   // profiling: event pairs per executed stage, accumulated on read
   struct Mark {
     int stage;
@@ -135,22 +143,38 @@ size_t pop_bytes(int prec) { return prec == LBEH_FP64 ? 8 : (prec == LBEH_FP32 ?
 // Stage `count` elements of the caller's buffer as FP64 on the device.
 // Returns a device pointer (the caller's own if it already is FP64 device
 // memory) and records temporaries in `tmp`.
+// A staging buffer of at least `bytes` for the current call, taken from the
+// handle's kept buffers (or allocated and kept); released by free_tmp.
+// Buffers above kStageKeep are freed after the call instead of kept.
+constexpr size_t kStageKeep = size_t(256) << 20;
+void *stage_buf(lbeh_handle *h, size_t bytes, std::vector<void *> &tmp) {
+  for (auto &b : h->stage)
+    if (!b.busy && b.bytes >= bytes) {
+      b.busy = true;
+      tmp.push_back(b.p);
+      return b.p;
+    }
+  void *p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) return nullptr;
+  h->stage.push_back({p, bytes, true});
+  tmp.push_back(p);
+  return p;
+}
+
 const double *stage_in(lbeh_handle *h, const void *src, int dtype, int on_device, long long count,
                        std::vector<void *> &tmp) {
   cudaStream_t s = h->c.s;
   if (on_device && dtype == LBEH_F64) return (const double *)src;
-  double *out = nullptr;
-  if (cudaMalloc(&out, count * 8) != cudaSuccess) return nullptr;
-  tmp.push_back(out);
+  double *out = (double *)stage_buf(h, count * 8, tmp);
+  if (!out) return nullptr;
   if (dtype == LBEH_F64) {
     cudaMemcpyAsync(out, src, count * 8, cudaMemcpyHostToDevice, s);
     return out;
   }
   const float *fsrc = (const float *)src;
   if (!on_device) {
-    float *fd = nullptr;
-    if (cudaMalloc(&fd, count * 4) != cudaSuccess) return nullptr;
-    tmp.push_back(fd);
+    float *fd = (float *)stage_buf(h, count * 4, tmp);
+    if (!fd) return nullptr;
     cudaMemcpyAsync(fd, src, count * 4, cudaMemcpyHostToDevice, s);
     fsrc = fd;
   }
@@ -168,8 +192,8 @@ bool stage_out(lbeh_handle *h, const double *dsrc, void *dst, int dtype, int on_
   }
   float *fd = (float *)dst;
   if (!on_device) {
-    if (cudaMalloc(&fd, count * 4) != cudaSuccess) return false;
-    tmp.push_back(fd);
+    fd = (float *)stage_buf(h, count * 4, tmp);
+    if (!fd) return false;
   }
   count_launch(), k_cvt<double, float><<<grid_for(count, 256), 256, 0, s>>>(dsrc, fd, count);
   if (!on_device) return cuda_ok(cudaMemcpyAsync(dst, fd, count * 4, cudaMemcpyDeviceToHost, s));
@@ -179,9 +203,8 @@ bool stage_out(lbeh_handle *h, const double *dsrc, void *dst, int dtype, int on_
 // FP64 device copy of a compute-type field.
 const double *as_f64(lbeh_handle *h, const void *src, long long count, std::vector<void *> &tmp) {
   if (h->c.prec == LBEH_FP64) return (const double *)src;
-  double *out = nullptr;
-  if (cudaMalloc(&out, count * 8) != cudaSuccess) return nullptr;
-  tmp.push_back(out);
+  double *out = (double *)stage_buf(h, count * 8, tmp);
+  if (!out) return nullptr;
   count_launch(), k_cvt<float, double><<<grid_for(count, 256), 256, 0, h->c.s>>>((const float *)src, out, count);
   return out;
 }
@@ -195,7 +218,17 @@ void to_compute(lbeh_handle *h, const double *src, void *dst, long long count) {
 
 void free_tmp(lbeh_handle *h, std::vector<void *> &tmp) {
   cudaStreamSynchronize(h->c.s);
-  for (void *t : tmp) cudaFree(t);
+  for (void *t : tmp)
+    for (size_t k = 0; k < h->stage.size(); ++k)
+      if (h->stage[k].p == t) {
+        if (h->stage[k].bytes > kStageKeep) {
+          cudaFree(t);
+          h->stage.erase(h->stage.begin() + (long)k);
+        } else {
+          h->stage[k].busy = false;
+        }
+        break;
+      }
   tmp.clear();
 }
 
@@ -616,6 +649,7 @@ static void destroy_handle(lbeh_handle *h) {
   poisson_destroy(h->pois);
   poisson_destroy(h->adj_pois);
   for (void *a : h->allocs) cudaFree(a);
+  for (auto &b : h->stage) cudaFree(b.p);
   delete h;
 }
 
@@ -648,7 +682,10 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
     h->hr[j] = in->cr[j];
     if (!(h->hr[j] > 0.0)) return LBEH_ERR_INVALID_ARG;
   }
-  drop_graphs(h);
+  // the captured step depends on the host-side configuration only through
+  // the colloid count (grids of the colloid kernels, the solid-node paths);
+  // the rest of what is loaded here lives in device memory
+  if (nc != c.ncoll || c.solids != (nc > 0)) drop_graphs(h);
   c.ncoll = nc;
   c.solids = nc > 0;
   if (nc) {
@@ -670,8 +707,8 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
   } else {
     std::vector<void *> t2;
     double *rd = nullptr;
-    if (cudaMalloc(&rd, 8 * c.ncomp * N) != cudaSuccess) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
-    tmp.push_back(rd);
+    rd = (decltype(rd))stage_buf(h, 8 * c.ncomp * N, tmp);
+    if (!rd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
     for (int s = 0; s < c.ncomp; ++s) {
       const double *r = stage_in(h, in->rho[s], in->dtype, in->on_device, N, tmp);
       if (!r) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
@@ -1128,17 +1165,16 @@ int lbeh_get_fields(lbeh_handle *h, lbeh_fields *out) {
   std::vector<void *> tmp;
   bool ok = true;
   if (out->rho[0] || out->rho[1]) {
-    double *rd = nullptr;
-    if (cudaMalloc(&rd, 8 * c.ncomp * N) != cudaSuccess) return LBEH_ERR_OOM;
-    tmp.push_back(rd);
+    double *rd = (double *)stage_buf(h, 8 * c.ncomp * N, tmp);
+    if (!rd) return LBEH_ERR_OOM;
     h->ops.get_rho(c, rd);
     for (int s = 0; s < c.ncomp; ++s)
       if (out->rho[s]) ok &= stage_out(h, rd + s * N, out->rho[s], out->dtype, out->on_device, N, tmp);
   }
   if (out->f) {
     double *fd = nullptr;
-    if (cudaMalloc(&fd, 8 * (size_t)c.ncomp * 19 * N) != cudaSuccess) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
-    tmp.push_back(fd);
+    fd = (decltype(fd))stage_buf(h, 8 * (size_t)c.ncomp * 19 * N, tmp);
+    if (!fd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
     h->ops.get_f(c, fd);
     ok &= stage_out(h, fd, out->f, out->dtype, out->on_device, (long long)c.ncomp * 19 * N, tmp);
   }
@@ -1153,8 +1189,8 @@ int lbeh_get_fields(lbeh_handle *h, lbeh_fields *out) {
   }
   if (out->phi) {
     double *pd = nullptr;
-    if (cudaMalloc(&pd, 8 * N) != cudaSuccess) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
-    tmp.push_back(pd);
+    pd = (decltype(pd))stage_buf(h, 8 * N, tmp);
+    if (!pd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
     phi_to_double(c, pd);
     ok &= stage_out(h, pd, out->phi, out->dtype, out->on_device, N, tmp);
   }

@@ -30,6 +30,7 @@
 #include <cuda.h>
 
 #include "internal.h"
+#include "dfloat.cuh"
 
 namespace lbeh {
 namespace {
@@ -93,22 +94,22 @@ __global__ void __launch_bounds__(kNABlock)
     k_obs_na(Dims d, int ncomp, int nions, const F *__restrict__ f, const F *__restrict__ n,
              const uint8_t *__restrict__ solid, const double *__restrict__ qc, double *__restrict__ scratch) {
   const long long N = d.N;
-  double acc[kNALen];
-#pragma unroll
-  for (int t = 0; t < kNALen; ++t) acc[t] = 0.0;
+  SumAcc<std::is_same<F, float>::value> acc[kNALen];
   const long long base = blockIdx.x * kNAChunk;
   for (int k = 0; k < kNAPerThread; ++k) {
     const long long i = base + (long long)k * kNABlock + threadIdx.x;
     if (i >= N) break;
     if (nions) {
-      const double np = double(n[i]), nm = double(n[N + i]);
-      acc[2] += np;
-      acc[3] += nm;
-      acc[4] += np - nm;
+      const F np = n[i], nm = n[N + i];
+      acc[2].add(np);
+      acc[3].add(nm);
+      acc[4].add(np);
+      acc[4].add(-nm);
     }
-    if (qc) acc[4] += qc[i];
+    if (qc) acc[4].add(F(qc[i]));
     if (solid && solid[i]) continue;
-    // per-site sums in the input's own precision, as the handle's reduction does
+    // per-site arithmetic of the handle's observables: sums in the input's own
+    // precision, running sums in double-float words (FP32) or FP64
     F rt[2] = {F(0), F(0)}, Jt[3] = {F(0), F(0), F(0)};
     for (int s = 0; s < ncomp; ++s)
 #pragma unroll
@@ -119,31 +120,29 @@ __global__ void __launch_bounds__(kNABlock)
         if (cy(q)) Jt[1] += F(cy(q)) * v;
         if (cz(q)) Jt[2] += F(cz(q)) * v;
       }
-    const double r[2] = {double(rt[0]), double(rt[1])};
-    const double J[3] = {double(Jt[0]), double(Jt[1]), double(Jt[2])};
-    acc[0] += r[0];
-    acc[1] += r[1];
-    acc[5] += J[0];
-    acc[6] += J[1];
-    acc[7] += J[2];
+    acc[0].add(rt[0]);
+    acc[1].add(rt[1]);
+    acc[5].add(Jt[0]);
+    acc[6].add(Jt[1]);
+    acc[7].add(Jt[2]);
     if (ncomp == 2) {
-      const double tot = r[0] + r[1];
-      const double c = tot > 0 ? (r[1] - r[0]) / tot : 0.0;
-      if (c > 0) {
+      const F tot = rt[0] + rt[1];
+      const F c = tot > F(0) ? (rt[1] - rt[0]) / tot : F(0);
+      if (c > F(0)) {
         int x, y, z;
         coords(d, i, x, y, z);
-        acc[8] += c;
-        acc[9] += c * x;
-        acc[10] += c * y;
-        acc[11] += c * z;
-        acc[12] += c * double(x) * x;
-        acc[13] += c * double(z) * z;
+        acc[8].add(c);
+        acc_prod(acc[9], c, F(x));
+        acc_prod(acc[10], c, F(y));
+        acc_prod(acc[11], c, F(z));
+        acc_prod2(acc[12], c, F(x));
+        acc_prod2(acc[13], c, F(z));
       }
     }
   }
   __shared__ double sh[kNALen][kNABlock];
 #pragma unroll
-  for (int t = 0; t < kNALen; ++t) sh[t][threadIdx.x] = acc[t];
+  for (int t = 0; t < kNALen; ++t) sh[t][threadIdx.x] = acc[t].get();
   __syncthreads();
   for (int w = kNABlock / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)

@@ -29,8 +29,34 @@ __global__ void __launch_bounds__(256) k_dot_partial(const double *__restrict__ 
   if (threadIdx.x == 0) part[blockIdx.x] = r;
 }
 
+// Up to kFinalLen values reduced together: every thread adds its strided
+// partials of all values (loads in flight together), then one shared-memory
+// tree over all values; longer lists one value at a time.  The order of the
+// additions per value is the same either way (fixed, deterministic).
+constexpr int kFinalLen = 16;
 __global__ void __launch_bounds__(256) k_final(const double *__restrict__ part, int nblocks, int len,
                                                double *__restrict__ out) {
+  if (len <= kFinalLen) {
+    __shared__ double shv[kFinalLen][256];
+    double acc[kFinalLen];
+#pragma unroll
+    for (int t = 0; t < kFinalLen; ++t) acc[t] = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += 256)
+#pragma unroll
+      for (int t = 0; t < kFinalLen; ++t)
+        if (t < len) acc[t] += part[(long long)b * len + t];
+#pragma unroll
+    for (int t = 0; t < kFinalLen; ++t) shv[t][threadIdx.x] = acc[t];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if (threadIdx.x < w)
+#pragma unroll
+        for (int t = 0; t < kFinalLen; ++t) shv[t][threadIdx.x] += shv[t][threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x < len) out[threadIdx.x] = shv[threadIdx.x][0];
+    return;
+  }
   __shared__ double sh[256];
   for (int t = 0; t < len; ++t) {
     double acc = 0.0;

@@ -13,6 +13,7 @@
 #pragma once
 
 #include "internal.h"
+#include "dfloat.cuh"
 
 namespace lbeh {
 
@@ -601,26 +602,28 @@ __global__ void k_get_rho(StepK<T> k, const S *__restrict__ f, double *__restric
 // ---------------------------------------------------------------- observables
 // Per-block FP64 partial sums, fixed order (block-strided sites, then a tree).
 // Layout: 0,1 mass; 2,3 ions; 4 charge; 5..7 momentum; 8 W; 9..11 W x,y,z;
-// 12 W x^2; 13 W z^2; 14,15 unused.
+// 12 W x^2; 13 W z^2; 14,15 unused.  Per thread the sums run in double-float
+// words in the FP32 modes (the FP64 rate of the target is a small fraction of
+// its FP32 rate) with the products W x, W x^2 formed exactly, in FP64 in the
+// FP64 mode; site indices are 32-bit (boxes below 2^31 sites).
 template <typename S, typename T, int NC>
 __global__ void __launch_bounds__(256) k_obs(StepK<T> k, const S *__restrict__ f, const T *__restrict__ n,
                                              const T *__restrict__ qc, const uint8_t *__restrict__ solid,
                                              double *__restrict__ partials) {
   const Dims d = k.d;
-  const long long N = d.N;
-  double acc[kObsLen];
-#pragma unroll
-  for (int t = 0; t < kObsLen; ++t) acc[t] = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-       i += (long long)gridDim.x * blockDim.x) {
+  const unsigned N = unsigned(d.N), nx = unsigned(d.nx), ny = unsigned(d.ny);
+  SumAcc<std::is_same<T, float>::value> acc[kObsLen];
+  const unsigned stride = gridDim.x * blockDim.x;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
     const bool sol = k.solids && solid[i];
     if (k.nions) {
-      const double np = double(n[i]), nm = double(n[N + i]);
-      acc[2] += np;
-      acc[3] += nm;
-      acc[4] += np - nm;
+      const T np = n[i], nm = n[N + i];
+      acc[2].add(np);
+      acc[3].add(nm);
+      acc[4].add(np);
+      acc[4].add(-nm);
     }
-    if (k.solids) acc[4] += double(qc[i]);
+    if (k.solids) acc[4].add(qc[i]);
     if (sol) continue;
     T rt[2] = {T(0), T(0)}, Jt[3] = {T(0), T(0), T(0)};
 #pragma unroll
@@ -633,32 +636,28 @@ __global__ void __launch_bounds__(256) k_obs(StepK<T> k, const S *__restrict__ f
         if (cy(qd)) Jt[1] += T(cy(qd)) * v;
         if (cz(qd)) Jt[2] += T(cz(qd)) * v;
       }
-    const double r[2] = {double(rt[0]), double(rt[1])};
-    const double J[3] = {double(Jt[0]), double(Jt[1]), double(Jt[2])};
-    acc[0] += r[0];
-    acc[1] += r[1];
-    acc[5] += J[0];
-    acc[6] += J[1];
-    acc[7] += J[2];
+    acc[0].add(rt[0]);
+    acc[1].add(rt[1]);
+    acc[5].add(Jt[0]);
+    acc[6].add(Jt[1]);
+    acc[7].add(Jt[2]);
     if (NC == 2) {
-      const double tot = r[0] + r[1];
-      const double c = tot > 0 ? (r[1] - r[0]) / tot : 0.0;
-      const double w = c > 0 ? c : 0.0;
-      if (w > 0) {
-        int x, y, z;
-        coords(d, i, x, y, z);
-        acc[8] += w;
-        acc[9] += w * x;
-        acc[10] += w * y;
-        acc[11] += w * z;
-        acc[12] += w * double(x) * x;
-        acc[13] += w * double(z) * z;
+      const T tot = rt[0] + rt[1];
+      const T c = tot > T(0) ? (rt[1] - rt[0]) / tot : T(0);
+      if (c > T(0)) {
+        const unsigned r = i / nx, x = i - r * nx, z = r / ny, y = r - z * ny;
+        acc[8].add(c);
+        acc_prod(acc[9], c, T(x));
+        acc_prod(acc[10], c, T(y));
+        acc_prod(acc[11], c, T(z));
+        acc_prod2(acc[12], c, T(x));
+        acc_prod2(acc[13], c, T(z));
       }
     }
   }
   __shared__ double sh[kObsLen][256];
 #pragma unroll
-  for (int t = 0; t < kObsLen; ++t) sh[t][threadIdx.x] = acc[t];
+  for (int t = 0; t < kObsLen; ++t) sh[t][threadIdx.x] = acc[t].get();
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w)
