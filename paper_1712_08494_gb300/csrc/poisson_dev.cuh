@@ -648,24 +648,37 @@ __device__ __forceinline__ void residual_site(const PArgs<T> &a, const Level<T> 
   const Faces<T> fc = faces(L0, i, ixp, ixm, iyp, iym, izp, izm);
   const T kxp = fc.xp, kxm = fc.xm, kyp = fc.yp, kym = fc.ym, kzp = fc.zp, kzm = fc.zm;
   if constexpr (DFM) {
+    // sum_k k_k (phi_k - phi_i): exact differences of the high words
+    // (two_sum) plus the differences of the low words, the high products
+    // exact with their FMA error terms, high parts summed with compensation
+    // (about 2^-46 of the largest flux term, as in general double-float
+    // arithmetic, at less than half its operations)
     const float *hi = a.phi_hi, *lo = a.phi_lo;
-    const DF p{hi[i], lo[i]};
-    DF Ap = df_mul_f(df_sub(DF{hi[ixp], lo[ixp]}, p), kxp);
-    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[ixm], lo[ixm]}, p), kxm));
-    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[iyp], lo[iyp]}, p), kyp));
-    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[iym], lo[iym]}, p), kym));
-    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[izp], lo[izp]}, p), kzp));
-    Ap = df_add(Ap, df_mul_f(df_sub(DF{hi[izm], lo[izm]}, p), kzm));
-    DF b = df_sub(qbar_df, DF{float(a.q[i]), 0.f});
+    const float h0 = hi[i], l0 = lo[i];
+    const unsigned nb[6] = {ixp, ixm, iyp, iym, izp, izm};
+    const float kk[6] = {float(kxp), float(kxm), float(kyp), float(kym), float(kzp), float(kzm)};
+    float ahi = 0.f, alo = 0.f;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const DF dd = two_sum(hi[nb[k]], -h0);
+      const float dlo = __fadd_rn(dd.lo, __fsub_rn(lo[nb[k]], l0));
+      const float prod = __fmul_rn(dd.hi, kk[k]);
+      const float plo = __fmaf_rn(dlo, kk[k], __fmaf_rn(dd.hi, kk[k], -prod));
+      const DF t = two_sum(ahi, prod);
+      ahi = t.hi;
+      alo = __fadd_rn(alo, __fadd_rn(t.lo, plo));
+    }
+    DF b = two_sum(qbar_df.hi, -float(a.q[i]));
+    b.lo = __fadd_rn(b.lo, qbar_df.lo);
     if (a.edf[0].hi != 0.f) b = df_add(b, df_mul(a.edf[0], two_sum(kxp, -kxm)));
     if (a.edf[1].hi != 0.f) b = df_add(b, df_mul(a.edf[1], two_sum(kyp, -kym)));
     if (a.edf[2].hi != 0.f) b = df_add(b, df_mul(a.edf[2], two_sum(kzp, -kzm)));
-    const DF r = df_sub(b, Ap);
-    const float rf = __fadd_rn(r.hi, r.lo);
+    const DF r = two_sum(b.hi, -ahi);
+    const float rf = __fadd_rn(r.hi, __fadd_rn(r.lo, __fsub_rn(b.lo, alo)));
     L0.b[i] = T(rf);
     ar.add(rf * rf);
     ab.add(b.hi * b.hi);
-    ap.add(p.hi);
+    ap.add(h0);
   } else {
     const double *phi = a.phi;
     const double p = phi[i];
