@@ -436,8 +436,9 @@ def run_ours(args):
         tr_p = ncu_poisson_traffic(cyc_solve)
     achieved_p = pois_bytes / t_pois / 1e9 if t_pois > 0 else 0.0
 
-    # whole-step roofline by the survey's rule: 340 + 16 s B/site (FP32, two
-    # components), s = Poisson fine-sweep equivalents of 16 B/site
+    # whole-step roofline: 340 B/site for the lattice passes (FP32, two
+    # components: macro, collide, Nernst-Planck) + 16 s B/site for the
+    # Poisson solve, s = its bytes expressed as 16-B/site sweep equivalents
     s_eq = pois_bytes / N / POISSON_BYTES_PER_SWEEP * (prof["calls"]["poisson"] / max(1, prof["calls"]["collide"]))
     step_bytes = 340 + POISSON_BYTES_PER_SWEEP * s_eq
     step_gbs = step_bytes * N * args.steps / (ms32 * 1e-3) / 1e9
@@ -552,8 +553,9 @@ def suspension_run(lbeh, stream, peak, peak_kind, args, n=256, steps=100):
         t_coll = prof["ms"]["collide"] / max(1, prof["calls"]["collide"]) * 1e-3
         gbs = collide_bytes(1, 4 if prec == "fp32" else 2, True) * n ** 3 / t_coll / 1e9
         total = sum(prof["ms"].values())
-        # whole-step roofline by the survey's rule: 172 + 16 s B/site (FP32) or
-        # 96 + 16 s (BF16) for one component, s = Poisson fine-sweep equivalents
+        # whole-step roofline: 172 B/site (FP32) or 96 (BF16) for the lattice
+        # passes of one component + 16 s B/site for the multigrid, s = fine
+        # sweeps per step
         sweeps = 2 * NU_SMOOTH * cycles / steps
         step_bytes = (172 if prec == "fp32" else 96) + POISSON_BYTES_PER_SWEEP * sweeps
         step_gbs = step_bytes * n ** 3 * steps / (ms * 1e-3) / 1e9
