@@ -116,7 +116,8 @@ typedef struct lbeh_fields {
   void *u;       /* [3][N] velocity for the equilibrium initialisation; get: physical velocity */
   void *f;       /* [ncomp][19][N] populations (set: overrides rho/u) */
   void *n[2];    /* cation, anion concentrations */
-  void *phi;     /* internal potential (set: warm start) */
+  void *phi;     /* internal potential (set: starting guess of the first solve; on an
+                    FP32 handle, FP32 values become the high word of the pair) */
   int ncolloid;  /* number of colloids (<= ncolloid_max) */
   double *cx;    /* [ncolloid][3] centres (x, y, z) */
   double *cv;    /* [ncolloid][3] velocities */

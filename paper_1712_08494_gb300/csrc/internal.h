@@ -84,7 +84,7 @@ struct PrecOps {
   void (*virt)(Ctx &);
   void (*collide)(Ctx &);
   void (*np)(Ctx &);
-  void (*obs_partials)(Ctx &, double *partials, int nblocks);  // kObsLen doubles per block
+  int (*obs_partials)(Ctx &, double *partials, int max_blocks);  // kObsLen doubles per block; returns the blocks
   void (*colloid_bb)(Ctx &);                                    // momentum exchange + electric force into cforce
   void (*remap)(Ctx &);                                         // node covering / uncovering after a move
 };

@@ -162,13 +162,13 @@ void *stage_buf(lbeh_handle *h, size_t bytes, std::vector<void *> &tmp) {
 }
 
 const double *stage_in(lbeh_handle *h, const void *src, int dtype, int on_device, long long count,
-                       std::vector<void *> &tmp) {
+                       std::vector<void *> &tmp, double *dst = nullptr) {
   cudaStream_t s = h->c.s;
-  if (on_device && dtype == LBEH_F64) return (const double *)src;
-  double *out = (double *)stage_buf(h, count * 8, tmp);
+  if (on_device && dtype == LBEH_F64 && !dst) return (const double *)src;
+  double *out = dst ? dst : (double *)stage_buf(h, count * 8, tmp);
   if (!out) return nullptr;
   if (dtype == LBEH_F64) {
-    cudaMemcpyAsync(out, src, count * 8, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(out, src, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
     return out;
   }
   const float *fsrc = (const float *)src;
@@ -214,6 +214,19 @@ void to_compute(lbeh_handle *h, const double *src, void *dst, long long count) {
     cudaMemcpyAsync(dst, src, count * 8, cudaMemcpyDeviceToDevice, h->c.s);
   else
     count_launch(), k_cvt<double, float><<<grid_for(count, 256), 256, 0, h->c.s>>>(src, (float *)dst, count);
+}
+
+// Load `count` values of the caller's array into a field held in the compute
+// type; FP32 input to an FP32 field is copied as it is, without an FP64 stage.
+bool load_compute(lbeh_handle *h, const void *src, int dtype, int on_device, long long count, void *dst,
+                  std::vector<void *> &tmp) {
+  if (h->c.prec != LBEH_FP64 && dtype == LBEH_F32)
+    return cuda_ok(cudaMemcpyAsync(dst, src, count * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                   h->c.s));
+  const double *d = stage_in(h, src, dtype, on_device, count, tmp);
+  if (!d) return false;
+  to_compute(h, d, dst, count);
+  return true;
 }
 
 void free_tmp(lbeh_handle *h, std::vector<void *> &tmp) {
@@ -709,11 +722,11 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
     double *rd = nullptr;
     rd = (decltype(rd))stage_buf(h, 8 * c.ncomp * N, tmp);
     if (!rd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
-    for (int s = 0; s < c.ncomp; ++s) {
-      const double *r = stage_in(h, in->rho[s], in->dtype, in->on_device, N, tmp);
-      if (!r) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
-      cudaMemcpyAsync(rd + s * N, r, 8 * N, cudaMemcpyDeviceToDevice, c.s);
-    }
+    for (int s = 0; s < c.ncomp; ++s)
+      if (!stage_in(h, in->rho[s], in->dtype, in->on_device, N, tmp, rd + s * N)) {
+        free_tmp(h, tmp);
+        return LBEH_ERR_OOM;
+      }
     const double *ud = nullptr;
     if (in->u) {
       ud = stage_in(h, in->u, in->dtype, in->on_device, 3 * N, tmp);
@@ -723,11 +736,12 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
   }
   // ions, zero on solid nodes
   if (c.nions) {
-    for (int s = 0; s < 2; ++s) {
-      const double *nd = stage_in(h, in->n[s], in->dtype, in->on_device, N, tmp);
-      if (!nd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
-      to_compute(h, nd, (char *)c.n[0] + (size_t)s * N * (c.prec == LBEH_FP64 ? 8 : 4), N);
-    }
+    for (int s = 0; s < 2; ++s)
+      if (!load_compute(h, in->n[s], in->dtype, in->on_device, N,
+                        (char *)c.n[0] + (size_t)s * N * (c.prec == LBEH_FP64 ? 8 : 4), tmp)) {
+        free_tmp(h, tmp);
+        return LBEH_ERR_OOM;
+      }
     if (c.solids) {
       if (c.prec == LBEH_FP64)
         count_launch(), k_mask_fluid<double><<<grid_for(N, 256), 256, 0, c.s>>>((double *)c.n[0], c.solid, N, 2);
@@ -736,10 +750,14 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
     }
   }
   // potential (warm start)
-  if (in->phi) {
-    const double *pd = stage_in(h, in->phi, in->dtype, in->on_device, N, tmp);
+  if (in->phi && !c.phi && in->dtype == LBEH_F32) {
+    // FP32 values are the high words of the double-float pair
+    cudaMemcpyAsync(c.phit, in->phi, 4 * N, in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.s);
+    cudaMemsetAsync(c.phi_lo, 0, 4 * N, c.s);
+  } else if (in->phi) {
+    const double *pd = stage_in(h, in->phi, in->dtype, in->on_device, N, tmp, c.phi);
     if (!pd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
-    phi_from_double(c, pd);
+    if (!c.phi) phi_from_double(c, pd);
   } else if (c.phi) {
     cudaMemsetAsync(c.phi, 0, 8 * N, c.s);
   } else {
@@ -841,9 +859,9 @@ const char *lbeh_last_error(lbeh_handle *h) { return h ? h->last_error : "no han
 // Fixed-order FP64 sums of the observables (layout of k_obs) on the host.
 static int obs_sums(lbeh_handle *h, double v[kObsLen]) {
   Ctx &c = h->c;
-  h->ops.obs_partials(c, c.red, kRedBlocks);
+  const int nb = h->ops.obs_partials(c, c.red, kRedBlocks);
   double *res = c.red + (size_t)kRedBlocks * kObsLen;
-  reduce_partials_final(c.red, kRedBlocks, kObsLen, res, c.s);
+  reduce_partials_final(c.red, nb, kObsLen, res, c.s);
   cudaMemcpyAsync(v, res, sizeof(double) * kObsLen, cudaMemcpyDeviceToHost, c.s);
   return cudaStreamSynchronize(c.s) == cudaSuccess ? LBEH_OK : LBEH_ERR_CUDA;
 }

@@ -754,10 +754,8 @@ int poisson_configure(Poisson *p, double tol, int max_iter, cudaStream_t s) {
 }
 
 int poisson_reset(Poisson *p, cudaStream_t s) {
-  // forget the previous solutions (new state loaded)
-  const int zero = 0;
-  if (cudaMemcpyAsync(&p->dev->have_prev, &zero, sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess) return -1;
-  return cudaStreamSynchronize(s) == cudaSuccess ? 0 : -1;
+  // forget the previous solutions (new state loaded); stream-ordered
+  return cudaMemsetAsync(&p->dev->have_prev, 0, sizeof(int), s) == cudaSuccess ? 0 : -1;
 }
 
 int poisson_solve(Poisson *p, Ctx &c, double *relres) {

@@ -600,72 +600,150 @@ __global__ void k_get_rho(StepK<T> k, const S *__restrict__ f, double *__restric
 }
 
 // ---------------------------------------------------------------- observables
-// Per-block FP64 partial sums, fixed order (block-strided sites, then a tree).
+// Per-block FP64 partial sums, fixed order (per thread, then a tree).
 // Layout: 0,1 mass; 2,3 ions; 4 charge; 5..7 momentum; 8 W; 9..11 W x,y,z;
 // 12 W x^2; 13 W z^2; 14,15 unused.  Per thread the sums run in double-float
 // words in the FP32 modes (the FP64 rate of the target is a small fraction of
 // its FP32 rate) with the products W x, W x^2 formed exactly, in FP64 in the
 // FP64 mode; site indices are 32-bit (boxes below 2^31 sites).
+//
+// The populations stream through shared memory: a block owns chunks of
+// kObsChunk consecutive sites (one per thread) and copies every population
+// row and both ion rows of its next chunk with 16-byte asynchronous copies
+// while it sums the current one, so each SM keeps whole chunks in flight
+// instead of the few loads a thread's registers can cover.  Boxes whose rows
+// do not start on 16-byte boundaries, and the sites past the last whole
+// chunk, are read directly.
+constexpr int kObsChunk = 256;
+
+template <typename S, typename T, int NC> struct ObsLayout {
+  static constexpr int kRows = NC * 19;
+  static constexpr int kPopBytes = kRows * kObsChunk * int(sizeof(S));
+  static constexpr int kBufBytes = kPopBytes + 2 * kObsChunk * int(sizeof(T));
+  static constexpr int kTreeBytes = kObsLen * kObsChunk * 8;
+  static constexpr int kSmem = 2 * kBufBytes > kTreeBytes ? 2 * kBufBytes : kTreeBytes;
+};
+
+__device__ __forceinline__ void obs_cp16(unsigned char *dst, const void *src) {
+  const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void obs_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void obs_wait_older() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void obs_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// copies of chunk sites [c0, c0 + kObsChunk): population row r to buf row r,
+// ion rows after the populations
 template <typename S, typename T, int NC>
-__global__ void __launch_bounds__(256) k_obs(StepK<T> k, const S *__restrict__ f, const T *__restrict__ n,
-                                             const T *__restrict__ qc, const uint8_t *__restrict__ solid,
-                                             double *__restrict__ partials) {
+__device__ __forceinline__ void obs_issue(unsigned char *buf, const S *__restrict__ f, const T *__restrict__ n,
+                                          unsigned N, unsigned c0, bool ions) {
+  using L = ObsLayout<S, T, NC>;
+  constexpr int PV = kObsChunk * int(sizeof(S)) / 16;  // 16-byte pieces of a population row
+  constexpr int IV = kObsChunk * int(sizeof(T)) / 16;
+  for (int e = threadIdx.x; e < L::kRows * PV; e += blockDim.x) {
+    const int r = e / PV, v = e - r * PV;
+    obs_cp16(buf + (r * kObsChunk) * int(sizeof(S)) + 16 * v,
+             reinterpret_cast<const unsigned char *>(f + (size_t)r * N + c0) + 16 * v);
+  }
+  if (ions)
+    for (int e = threadIdx.x; e < 2 * IV; e += blockDim.x) {
+      const int r = e / IV, v = e - r * IV;
+      obs_cp16(buf + L::kPopBytes + (r * kObsChunk) * int(sizeof(T)) + 16 * v,
+               reinterpret_cast<const unsigned char *>(n + (size_t)r * N + c0) + 16 * v);
+    }
+}
+
+// one site's contributions; pop(s, q) is population q of component s
+template <typename T, int NC, class Acc, class Pop>
+__device__ __forceinline__ void obs_site(Acc *acc, const StepK<T> &k, unsigned i, unsigned nx, unsigned ny, bool sol,
+                                         T np, T nm, T qcv, const Pop &pop) {
+  if (k.nions) {
+    acc[2].add(np);
+    acc[3].add(nm);
+    acc[4].add(np);
+    acc[4].add(-nm);
+  }
+  if (k.solids) acc[4].add(qcv);
+  if (sol) return;
+  T rt[2] = {T(0), T(0)}, Jt[3] = {T(0), T(0), T(0)};
+#pragma unroll
+  for (int s = 0; s < NC; ++s)
+#pragma unroll
+    for (int qd = 0; qd < 19; ++qd) {
+      const T v = pop(s, qd);
+      rt[s] += v;
+      if (cx(qd)) Jt[0] += T(cx(qd)) * v;
+      if (cy(qd)) Jt[1] += T(cy(qd)) * v;
+      if (cz(qd)) Jt[2] += T(cz(qd)) * v;
+    }
+  acc[0].add(rt[0]);
+  acc[1].add(rt[1]);
+  acc[5].add(Jt[0]);
+  acc[6].add(Jt[1]);
+  acc[7].add(Jt[2]);
+  if (NC == 2) {
+    const T tot = rt[0] + rt[1];
+    const T c = tot > T(0) ? (rt[1] - rt[0]) / tot : T(0);
+    if (c > T(0)) {
+      const unsigned r = i / nx, x = i - r * nx, z = r / ny, y = r - z * ny;
+      acc[8].add(c);
+      acc_prod(acc[9], c, T(x));
+      acc_prod(acc[10], c, T(y));
+      acc_prod(acc[11], c, T(z));
+      acc_prod2(acc[12], c, T(x));
+      acc_prod2(acc[13], c, T(z));
+    }
+  }
+}
+
+// blockDim.x == kObsChunk; nfull whole chunks are staged (0: none)
+template <typename S, typename T, int NC>
+__global__ void __launch_bounds__(kObsChunk) k_obs(StepK<T> k, const S *__restrict__ f, const T *__restrict__ n,
+                                                   const T *__restrict__ qc, const uint8_t *__restrict__ solid,
+                                                   double *__restrict__ partials, unsigned nfull) {
+  using L = ObsLayout<S, T, NC>;
+  extern __shared__ __align__(16) unsigned char obs_sm[];
   const Dims d = k.d;
   const unsigned N = unsigned(d.N), nx = unsigned(d.nx), ny = unsigned(d.ny);
+  const bool ions = k.nions != 0;
   SumAcc<std::is_same<T, float>::value> acc[kObsLen];
-  const unsigned stride = gridDim.x * blockDim.x;
-  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += stride) {
-    const bool sol = k.solids && solid[i];
-    if (k.nions) {
-      const T np = n[i], nm = n[N + i];
-      acc[2].add(np);
-      acc[3].add(nm);
-      acc[4].add(np);
-      acc[4].add(-nm);
-    }
-    if (k.solids) acc[4].add(qc[i]);
-    if (sol) continue;
-    T rt[2] = {T(0), T(0)}, Jt[3] = {T(0), T(0), T(0)};
-#pragma unroll
-    for (int s = 0; s < NC; ++s)
-#pragma unroll
-      for (int qd = 0; qd < 19; ++qd) {
-        const T v = Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]);
-        rt[s] += v;
-        if (cx(qd)) Jt[0] += T(cx(qd)) * v;
-        if (cy(qd)) Jt[1] += T(cy(qd)) * v;
-        if (cz(qd)) Jt[2] += T(cz(qd)) * v;
-      }
-    acc[0].add(rt[0]);
-    acc[1].add(rt[1]);
-    acc[5].add(Jt[0]);
-    acc[6].add(Jt[1]);
-    acc[7].add(Jt[2]);
-    if (NC == 2) {
-      const T tot = rt[0] + rt[1];
-      const T c = tot > T(0) ? (rt[1] - rt[0]) / tot : T(0);
-      if (c > T(0)) {
-        const unsigned r = i / nx, x = i - r * nx, z = r / ny, y = r - z * ny;
-        acc[8].add(c);
-        acc_prod(acc[9], c, T(x));
-        acc_prod(acc[10], c, T(y));
-        acc_prod(acc[11], c, T(z));
-        acc_prod2(acc[12], c, T(x));
-        acc_prod2(acc[13], c, T(z));
-      }
-    }
+  const unsigned t = threadIdx.x;
+  unsigned c = blockIdx.x;
+  if (c < nfull) obs_issue<S, T, NC>(obs_sm, f, n, N, c * kObsChunk, ions);
+  obs_commit();
+  for (int b = 0; c < nfull; c += gridDim.x, b ^= 1) {
+    unsigned char *cur = obs_sm + b * L::kBufBytes, *nxt = obs_sm + (b ^ 1) * L::kBufBytes;
+    if (c + gridDim.x < nfull) obs_issue<S, T, NC>(nxt, f, n, N, (c + gridDim.x) * kObsChunk, ions);
+    obs_commit();
+    obs_wait_older();  // chunk c has landed
+    __syncthreads();
+    const S *ps = reinterpret_cast<const S *>(cur);
+    const T *ns = reinterpret_cast<const T *>(cur + L::kPopBytes);
+    const unsigned i = c * kObsChunk + t;
+    obs_site<T, NC>(acc, k, i, nx, ny, k.solids && solid[i], ions ? ns[t] : T(0), ions ? ns[kObsChunk + t] : T(0),
+                    k.solids ? qc[i] : T(0), [&](int s, int qd) {
+                      return Store<S, T>::ldc(ps, (s * 19 + qd) * kObsChunk + t, wq<T>(qd) * k.shift[s]);
+                    });
+    __syncthreads();  // buffer cur is refilled in the next iteration
   }
-  __shared__ double sh[kObsLen][256];
-#pragma unroll
-  for (int t = 0; t < kObsLen; ++t) sh[t][threadIdx.x] = acc[t].get();
+  obs_wait_all();
+  for (unsigned i = nfull * kObsChunk + blockIdx.x * kObsChunk + t; i < N; i += gridDim.x * kObsChunk)
+    obs_site<T, NC>(acc, k, i, nx, ny, k.solids && solid[i], ions ? n[i] : T(0), ions ? n[N + i] : T(0),
+                    k.solids ? qc[i] : T(0), [&](int s, int qd) {
+                      return Store<S, T>::ld(f, (size_t)(s * 19 + qd) * N + i, wq<T>(qd) * k.shift[s]);
+                    });
   __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w)
+  double(*sh)[kObsChunk] = reinterpret_cast<double(*)[kObsChunk]>(obs_sm);
 #pragma unroll
-      for (int t = 0; t < kObsLen; ++t) sh[t][threadIdx.x] += sh[t][threadIdx.x + w];
+  for (int m = 0; m < kObsLen; ++m) sh[m][t] = acc[m].get();
+  __syncthreads();
+  for (int w = kObsChunk / 2; w > 0; w >>= 1) {
+    if (t < unsigned(w))
+#pragma unroll
+      for (int m = 0; m < kObsLen; ++m) sh[m][t] += sh[m][t + w];
     __syncthreads();
   }
-  if (threadIdx.x < kObsLen) partials[blockIdx.x * kObsLen + threadIdx.x] = sh[threadIdx.x][0];
+  if (t < unsigned(kObsLen)) partials[blockIdx.x * kObsLen + t] = sh[t][0];
 }
 
 // ---------------------------------------------------------------- colloid momentum exchange
@@ -969,13 +1047,37 @@ template <typename S, typename T> struct Launch {
     else
       count_launch(), k_np<T, false><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, n, nn, (const T *)c.flux, (const T *)c.u, c.solid);
   }
-  static void obs_partials(Ctx &c, double *partials, int nblocks) {
-    auto k = make_stepk<T>(c);
+  // one resident wave of k_obs (at most max_blocks); returns its block count
+  template <int NC> static int obs_launch(Ctx &c, double *partials, int max_blocks) {
+    using L = ObsLayout<S, T, NC>;
+    static int per_dev[64];  // resident blocks per SM, by device ordinal (0: not yet known)
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int per = dev >= 0 && dev < 64 ? per_dev[dev] : 0;
+    if (per == 0) {
+      cudaFuncSetAttribute(k_obs<S, T, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::kSmem);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_obs<S, T, NC>, kObsChunk, L::kSmem) != cudaSuccess ||
+          per < 1) {
+        cudaGetLastError();
+        per = 1;
+      }
+      if (dev >= 0 && dev < 64) per_dev[dev] = per;
+    }
+    const int nb = std::max(1, std::min(max_blocks, per * std::max(1, nsm)));
     const S *f = (const S *)c.f[c.cur];
-    if (c.ncomp == 2)
-      count_launch(), k_obs<S, T, 2><<<nblocks, B, 0, c.s>>>(k, f, (const T *)c.n[c.ncur], (const T *)c.qc, c.solid, partials);
-    else
-      count_launch(), k_obs<S, T, 1><<<nblocks, B, 0, c.s>>>(k, f, (const T *)c.n[c.ncur], (const T *)c.qc, c.solid, partials);
+    const T *n = (const T *)c.n[c.ncur];
+    const unsigned N = unsigned(c.d.N);
+    // 16-byte copies need every row to start on a 16-byte boundary
+    const bool aligned = (size_t(N) * sizeof(S)) % 16 == 0 && (size_t(N) * sizeof(T)) % 16 == 0 &&
+                         reinterpret_cast<uintptr_t>(f) % 16 == 0 && (!c.nions || reinterpret_cast<uintptr_t>(n) % 16 == 0);
+    const unsigned nfull = aligned ? N / kObsChunk : 0u;
+    count_launch(), k_obs<S, T, NC><<<nb, kObsChunk, L::kSmem, c.s>>>(make_stepk<T>(c), f, n, (const T *)c.qc, c.solid,
+                                                                       partials, nfull);
+    return nb;
+  }
+  static int obs_partials(Ctx &c, double *partials, int max_blocks) {
+    return c.ncomp == 2 ? obs_launch<2>(c, partials, max_blocks) : obs_launch<1>(c, partials, max_blocks);
   }
   static void colloid_bb(Ctx &c) {
     if (!c.solids || c.ncoll == 0) return;

@@ -132,6 +132,91 @@ def test_reduced_precision_droplet(lbeh, prec, tol_rho):
     sg.close()
 
 
+@pytest.mark.parametrize("prec,src", [("fp64", "host64"), ("fp32", "host32"), ("fp32", "device32")])
+def test_restart_with_potential(lbeh, prec, src):
+    """A state loaded together with its potential: n and phi read back exactly
+    as loaded, the first solve starts from the loaded potential (fewer
+    iterations than from zero) and the step matches the oracle started from
+    the same state and potential."""
+    import torch
+    from oracle import OracleSystem
+    w = synth.droplet(n=24, r=7.0, prec=prec, tol=1e-13 if prec == "fp64" else 1e-10, Ez=0.02, charge=5.0,
+                      salt=2e-3)
+    sg = gpu_for(w, lbeh)
+    sg.step(5)
+    ck = sg.get(("rho", "n", "phi"))
+    sg.close()
+    dt = np.float64 if src == "host64" else np.float32
+    arrs = [np.ascontiguousarray(a, dtype=dt) for a in (ck["rho"][0], ck["rho"][1], ck["n"][0], ck["n"][1], ck["phi"])]
+    exact = [a.astype(np.float64) for a in arrs]
+    if src == "device32":
+        arrs = [torch.from_numpy(a).cuda() for a in arrs]
+    cycles = {}
+    for warm in (False, True):
+        sg = lbeh.System(w.params, 0)
+        sg.set_fields(rho=arrs[:2], n=arrs[2:4], phi=arrs[4] if warm else None)
+        if warm:
+            got = sg.get(("rho", "n", "phi"))
+            assert np.array_equal(got["n"], np.stack(exact[2:4]))
+            assert np.array_equal(got["phi"], exact[4])
+            assert rel_err(got["rho"], np.stack(exact[:2])) < (1e-14 if prec == "fp64" else 1e-6)
+        sg.profile_enable(False)
+        assert sg.step(1) == 0
+        cycles[warm] = sg.profile_read()["poisson_cycles"]
+        if warm:
+            so = OracleSystem(w.params, np.stack(exact[:2]), np.stack(exact[2:4]), phi=exact[4])
+            so.step()
+            errs = compare(sg, so, ("rho", "n", "phi"))
+            if prec == "fp64":
+                assert max(errs.values()) < 1e-11, errs
+            else:
+                assert errs["rho"] < 2e-5 and errs["n"] < 2e-5 and errs["phi"] < 2e-4, errs
+        sg.close()
+    assert cycles[True] < cycles[False], cycles
+
+
+@pytest.mark.parametrize("case", ["droplet_fp64", "slab_fp32_tail", "odd_fp32"])
+def test_observables_match_their_definition(lbeh, case):
+    """lbeh_observables against its sums written out in FP64 over the state read
+    back: whole staged chunks of 256 sites (24^3), whole chunks plus a ragged
+    tail and a colloid (20x24x28), and a box whose rows are not 16-byte
+    aligned (13x11x9), which is read directly."""
+    from oracle import observables
+    from oracle.lattice import C
+    if case == "droplet_fp64":
+        w = synth.droplet(n=24, r=7.0, prec="fp64", tol=1e-12, Ez=0.02, charge=5.0, salt=2e-3)
+    elif case == "slab_fp32_tail":
+        w = _slab(prec="fp32", tol=1e-8)
+    else:
+        w = synth.two_slab(nx=13, ny=11, nz=9, G=4.0, prec="fp32", tol=1e-8, colloid=False)
+    sg = gpu_for(w, lbeh)
+    sg.step(3)
+    o = sg.observables()
+    st = sg.get(("rho", "n"), f=True)
+    f = st["f"]
+    fl = np.ones(f.shape[2:], dtype=bool)
+    qc_sum = 0.0
+    if len(w.colloid_r):
+        fl = sg.aux(lbeh.LBEH_AUX_SOLID) == 0
+        qc_sum = float(sg.aux(lbeh.LBEH_AUX_QC).sum())
+    rho = f.sum(axis=1) * fl
+    mass = [float(rho[s].sum()) for s in range(f.shape[0])]
+    ions = [float(st["n"][s].sum()) for s in range(2)]
+    mom = sum(C[q] * float((f[:, q] * fl).sum()) for q in range(1, 19))
+    D, centroid = observables.deformation(rho)
+    rel = 1e-12 if case == "droplet_fp64" else 1e-6  # FP32 site sums: 19 roundings of 2^-24 each
+    ms, js = sum(mass), sum(ions)
+    for s in range(2):
+        assert abs(o.mass[s] - mass[s]) <= rel * ms, (s, o.mass[s], mass[s])
+        assert abs(o.ions[s] - ions[s]) <= rel * js, (s, o.ions[s], ions[s])
+    assert abs(o.charge - (ions[0] - ions[1] + qc_sum)) <= rel * (js + abs(qc_sum))
+    for a in range(3):
+        assert abs(o.momentum[a] - mom[a]) <= rel * ms, (a, o.momentum[a], mom[a])
+        assert abs(o.centroid[a] - centroid[a]) <= (1e-10 if rel < 1e-9 else 1e-4), (a, o.centroid[a], centroid[a])
+    assert abs(o.deformation - D) <= (1e-10 if rel < 1e-9 else 1e-5), (o.deformation, D)
+    sg.close()
+
+
 def test_fp32_two_slab_with_colloid(lbeh):
     w = _slab(prec="fp32", tol=1e-10)
     so = oracle_for(w)
