@@ -210,6 +210,7 @@ template <typename T> static void build(Ctx &c) {
     count_launch(), k_charge<T><<<c.ncoll, 256, 0, c.s>>>(c.d, c.cx, c.cr, c.cq, c.surface, c.owner, c.ccount, (T *)c.qc);
   }
   count_launch(), k_psi_f<T><<<grid_for(N, 256), 256, 0, c.s>>>(N, c.solid, (const T *)c.psi_s, (T *)c.psi_f);
+  c.geom_empty = c.ncoll == 0;
 }
 
 void geometry_build(Ctx &c) {

@@ -23,6 +23,7 @@ struct Ctx {
   Dims d;
   int ncomp = 1, nions = 0, prec = LBEH_FP32;
   bool solids = false;      // colloids present
+  bool geom_empty = false;  // geometry arrays hold the empty geometry (no colloids)
   bool has_field = false;   // potential or applied field present
   bool solvation = false;   // dmu != 0
   double tau = 1, G = 0, D = 0;
@@ -76,7 +77,8 @@ struct Ctx {
 
 // Per-storage-type kernels (defined in step_<prec>.cu).
 struct PrecOps {
-  void (*init_eq)(Ctx &, const double *rho, const double *u);  // rho [ncomp][N], u [3][N] or null (FP64 device)
+  // rho [ncomp][N], u [3][N] or null: device arrays, FP32 if f32 else FP64
+  void (*init_eq)(Ctx &, const void *rho, const void *u, int f32);
   void (*init_f)(Ctx &, const double *f);                      // [ncomp][19][N] FP64 device
   void (*get_f)(Ctx &, double *f);                             // [ncomp][19][N] FP64 device
   void (*get_rho)(Ctx &, double *rho);                         // [ncomp][N] FP64 device

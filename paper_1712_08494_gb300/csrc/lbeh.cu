@@ -51,6 +51,13 @@ struct lbeh_handle {
   // whole-step CUDA graphs, one per ping-pong parity
   cudaStream_t gs = nullptr;           // capture / replay stream
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // host-to-device copies run on their own stream; work issued on the
+  // handle's stream after a copy waits for it (ev_cp), so conversions of the
+  // first inputs overlap the copies of the later ones
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_fence = nullptr, ev_cp = nullptr;
+  bool fenced = false;  // cs already ordered after the work issued on the handle's stream
+  bool copied = false;  // ev_cp marks copies the host has not yet waited for
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   bool graphs_ready = false;
   bool eager = false;                  // LBEH_EAGER=1 disables graphs
@@ -161,6 +168,32 @@ void *stage_buf(lbeh_handle *h, size_t bytes, std::vector<void *> &tmp) {
   return p;
 }
 
+// Host-to-device copy on the copy stream, ordered after the work already
+// issued on the handle's stream (once per set call, else before each copy);
+// work issued on the handle's stream afterwards waits for the copy.
+void h2d(lbeh_handle *h, void *dst, const void *src, size_t bytes) {
+  if (!h->cs) {  // handle without a copy stream: in order on its own stream
+    cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->c.s);
+    return;
+  }
+  if (!h->fenced) {
+    cudaEventRecord(h->ev_fence, h->c.s);
+    cudaStreamWaitEvent(h->cs, h->ev_fence, 0);
+  }
+  cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, h->cs);
+  cudaEventRecord(h->ev_cp, h->cs);
+  cudaStreamWaitEvent(h->c.s, h->ev_cp, 0);
+  h->copied = true;
+}
+
+// host or device source into device memory
+void copy_in(lbeh_handle *h, void *dst, const void *src, size_t bytes, int on_device) {
+  if (on_device)
+    cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, h->c.s);
+  else
+    h2d(h, dst, src, bytes);
+}
+
 const double *stage_in(lbeh_handle *h, const void *src, int dtype, int on_device, long long count,
                        std::vector<void *> &tmp, double *dst = nullptr) {
   cudaStream_t s = h->c.s;
@@ -168,14 +201,14 @@ const double *stage_in(lbeh_handle *h, const void *src, int dtype, int on_device
   double *out = dst ? dst : (double *)stage_buf(h, count * 8, tmp);
   if (!out) return nullptr;
   if (dtype == LBEH_F64) {
-    cudaMemcpyAsync(out, src, count * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s);
+    copy_in(h, out, src, count * 8, on_device);
     return out;
   }
   const float *fsrc = (const float *)src;
   if (!on_device) {
     float *fd = (float *)stage_buf(h, count * 4, tmp);
     if (!fd) return nullptr;
-    cudaMemcpyAsync(fd, src, count * 4, cudaMemcpyHostToDevice, s);
+    h2d(h, fd, src, count * 4);
     fsrc = fd;
   }
   count_launch(), k_cvt<float, double><<<grid_for(count, 256), 256, 0, s>>>(fsrc, out, count);
@@ -220,17 +253,22 @@ void to_compute(lbeh_handle *h, const double *src, void *dst, long long count) {
 // type; FP32 input to an FP32 field is copied as it is, without an FP64 stage.
 bool load_compute(lbeh_handle *h, const void *src, int dtype, int on_device, long long count, void *dst,
                   std::vector<void *> &tmp) {
-  if (h->c.prec != LBEH_FP64 && dtype == LBEH_F32)
-    return cuda_ok(cudaMemcpyAsync(dst, src, count * 4, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                   h->c.s));
+  if (h->c.prec != LBEH_FP64 && dtype == LBEH_F32) {
+    copy_in(h, dst, src, count * 4, on_device);
+    return true;
+  }
   const double *d = stage_in(h, src, dtype, on_device, count, tmp);
   if (!d) return false;
   to_compute(h, d, dst, count);
   return true;
 }
 
-void free_tmp(lbeh_handle *h, std::vector<void *> &tmp) {
-  cudaStreamSynchronize(h->c.s);
+// Return staged buffers to the pool.  Without wait, the work still queued on
+// the handle's stream may read them: every later use is ordered after it
+// (same stream, or the copy stream behind a fence), and cudaFree of the
+// large ones synchronises the device.
+void free_tmp(lbeh_handle *h, std::vector<void *> &tmp, bool wait = true) {
+  if (wait) cudaStreamSynchronize(h->c.s);
   for (void *t : tmp)
     for (size_t k = 0; k < h->stage.size(); ++k)
       if (h->stage[k].p == t) {
@@ -496,6 +534,9 @@ int lbeh_create(const lbeh_params *p, lbeh_handle **out) {
   ok &= cudaStreamCreateWithFlags(&h->gs, cudaStreamNonBlocking) == cudaSuccess;
   ok &= cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) == cudaSuccess;
   ok &= cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming) == cudaSuccess;
+  ok &= cudaStreamCreateWithFlags(&h->cs, cudaStreamNonBlocking) == cudaSuccess;
+  ok &= cudaEventCreateWithFlags(&h->ev_fence, cudaEventDisableTiming) == cudaSuccess;
+  ok &= cudaEventCreateWithFlags(&h->ev_cp, cudaEventDisableTiming) == cudaSuccess;
   {
     const char *e = getenv("LBEH_EAGER");
     h->eager = e && e[0] == '1';
@@ -659,6 +700,12 @@ static void destroy_handle(lbeh_handle *h) {
   }
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->cs) {
+    cudaStreamSynchronize(h->cs);
+    cudaStreamDestroy(h->cs);
+  }
+  if (h->ev_fence) cudaEventDestroy(h->ev_fence);
+  if (h->ev_cp) cudaEventDestroy(h->ev_cp);
   poisson_destroy(h->pois);
   poisson_destroy(h->adj_pois);
   for (void *a : h->allocs) cudaFree(a);
@@ -708,7 +755,24 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
     cudaMemcpyAsync(c.cr, h->hr.data(), 8 * nc, cudaMemcpyHostToDevice, c.s);
     cudaMemsetAsync(c.cforce, 0, 8 * 3 * nc, c.s);
   }
-  geometry_build(c);
+  if (nc > 0 || !c.geom_empty) geometry_build(c);  // no colloids before or now: nothing to rebuild
+
+  // the host arrays go out on the copy stream behind one fence; what does
+  // not depend on them is issued first, so that it overlaps the copies
+  cudaEventRecord(h->ev_fence, c.s);
+  cudaStreamWaitEvent(h->cs, h->ev_fence, 0);
+  h->fenced = true;
+  struct Unfence {
+    lbeh_handle *h;
+    ~Unfence() { h->fenced = false; }
+  } unfence{h};
+  cudaMemsetAsync(c.u, 0, (c.prec == LBEH_FP64 ? 8 : 4) * 3 * N, c.s);
+  cudaMemsetAsync(c.status, 0, sizeof(int), c.s);
+  if (h->pois && poisson_reset(h->pois, c.s) != 0) return LBEH_ERR_CUDA;
+  const bool phi_hi_only = in->phi && !c.phi && in->dtype == LBEH_F32;
+  if (!in->phi && c.phi) cudaMemsetAsync(c.phi, 0, 8 * N, c.s);
+  if (!in->phi && !c.phi) cudaMemsetAsync(c.phit, 0, 4 * N, c.s);
+  if ((!in->phi && !c.phi) || phi_hi_only) cudaMemsetAsync(c.phi_lo, 0, 4 * N, c.s);
 
   // populations
   c.cur = 0;
@@ -717,10 +781,21 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
     const double *fd = stage_in(h, in->f, in->dtype, in->on_device, (long long)c.ncomp * 19 * N, tmp);
     if (!fd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
     h->ops.init_f(c, fd);
+  } else if (in->dtype == LBEH_F32) {
+    // FP32 densities (and velocities) feed the equilibrium directly
+    float *rd = (float *)stage_buf(h, 4 * c.ncomp * N, tmp);
+    if (!rd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
+    for (int s = 0; s < c.ncomp; ++s) copy_in(h, rd + s * N, in->rho[s], 4 * N, in->on_device);
+    const float *ud = (const float *)in->u;
+    if (in->u && !in->on_device) {
+      float *st = (float *)stage_buf(h, 4 * 3 * N, tmp);
+      if (!st) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
+      h2d(h, st, in->u, 4 * 3 * N);
+      ud = st;
+    }
+    h->ops.init_eq(c, rd, ud, 1);
   } else {
-    std::vector<void *> t2;
-    double *rd = nullptr;
-    rd = (decltype(rd))stage_buf(h, 8 * c.ncomp * N, tmp);
+    double *rd = (double *)stage_buf(h, 8 * c.ncomp * N, tmp);
     if (!rd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
     for (int s = 0; s < c.ncomp; ++s)
       if (!stage_in(h, in->rho[s], in->dtype, in->on_device, N, tmp, rd + s * N)) {
@@ -732,7 +807,7 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
       ud = stage_in(h, in->u, in->dtype, in->on_device, 3 * N, tmp);
       if (!ud) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
     }
-    h->ops.init_eq(c, rd, ud);
+    h->ops.init_eq(c, rd, ud, 0);
   }
   // ions, zero on solid nodes
   if (c.nions) {
@@ -749,35 +824,29 @@ int lbeh_set_fields(lbeh_handle *h, const lbeh_fields *in) {
         count_launch(), k_mask_fluid<float><<<grid_for(N, 256), 256, 0, c.s>>>((float *)c.n[0], c.solid, N, 2);
     }
   }
-  // potential (warm start)
-  if (in->phi && !c.phi && in->dtype == LBEH_F32) {
+  // potential: the starting guess of the first solve
+  if (phi_hi_only) {
     // FP32 values are the high words of the double-float pair
-    cudaMemcpyAsync(c.phit, in->phi, 4 * N, in->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c.s);
-    cudaMemsetAsync(c.phi_lo, 0, 4 * N, c.s);
+    copy_in(h, c.phit, in->phi, 4 * N, in->on_device);
   } else if (in->phi) {
     const double *pd = stage_in(h, in->phi, in->dtype, in->on_device, N, tmp, c.phi);
     if (!pd) { free_tmp(h, tmp); return LBEH_ERR_OOM; }
     if (!c.phi) phi_from_double(c, pd);
-  } else if (c.phi) {
-    cudaMemsetAsync(c.phi, 0, 8 * N, c.s);
-  } else {
-    cudaMemsetAsync(c.phit, 0, 4 * N, c.s);
-    cudaMemsetAsync(c.phi_lo, 0, 4 * N, c.s);
-  }
-  cudaMemsetAsync(c.u, 0, (c.prec == LBEH_FP64 ? 8 : 4) * 3 * N, c.s);
-  cudaMemsetAsync(c.status, 0, sizeof(int), c.s);
-  if (h->pois && poisson_reset(h->pois, c.s) != 0) {
-    free_tmp(h, tmp);
-    return LBEH_ERR_CUDA;
   }
   h->status = LBEH_OK;
   h->steps = 0;
   h->last_iters = 0;
   h->last_relres = 0.0;
   h->loaded = true;
+  // synchronous with respect to the host arrays: their copies have ended;
+  // the conversions queued on the stream may still run
+  if (h->copied) {
+    cudaEventSynchronize(h->ev_cp);
+    h->copied = false;
+  }
   const cudaError_t e = cudaGetLastError();
-  free_tmp(h, tmp);
-  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return LBEH_ERR_CUDA;
+  free_tmp(h, tmp, false);
+  if (e != cudaSuccess) return LBEH_ERR_CUDA;
   return LBEH_OK;
 }
 

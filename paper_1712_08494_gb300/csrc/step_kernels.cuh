@@ -529,9 +529,9 @@ __global__ void __launch_bounds__(256) k_np(StepK<T> k, const T *__restrict__ n,
 }
 
 // ---------------------------------------------------------------- init / read-out
-template <typename S, typename T, int NC>
-__global__ void k_init_eq(StepK<T> k, S *__restrict__ f, const double *__restrict__ rho,
-                          const double *__restrict__ u, const uint8_t *__restrict__ solid) {
+template <typename S, typename T, int NC, typename R>
+__global__ void k_init_eq(StepK<T> k, S *__restrict__ f, const R *__restrict__ rho, const R *__restrict__ u,
+                          const uint8_t *__restrict__ solid) {
   const long long N = k.d.N;
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i >= N) return;
@@ -965,13 +965,19 @@ __global__ void __launch_bounds__(256) k_remap_ions(StepK<T> k, T *__restrict__ 
 template <typename S, typename T> struct Launch {
   static constexpr int B = 256;
 
-  static void init_eq(Ctx &c, const double *rho, const double *u) {
+  template <typename R> static void init_eq_from(Ctx &c, const R *rho, const R *u) {
     auto k = make_stepk<T>(c);
     S *f = (S *)c.f[c.cur];
     if (c.ncomp == 2)
-      count_launch(), k_init_eq<S, T, 2><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, rho, u, c.solid);
+      count_launch(), k_init_eq<S, T, 2, R><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, rho, u, c.solid);
     else
-      count_launch(), k_init_eq<S, T, 1><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, rho, u, c.solid);
+      count_launch(), k_init_eq<S, T, 1, R><<<grid_for(c.d.N, B), B, 0, c.s>>>(k, f, rho, u, c.solid);
+  }
+  static void init_eq(Ctx &c, const void *rho, const void *u, int f32) {
+    if (f32)
+      init_eq_from<float>(c, (const float *)rho, (const float *)u);
+    else
+      init_eq_from<double>(c, (const double *)rho, (const double *)u);
   }
   static void init_f(Ctx &c, const double *src) {
     auto k = make_stepk<T>(c);
