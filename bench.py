@@ -471,11 +471,15 @@ def run_ours(args):
         return
     extra = {}
     if not args.no_extra:
-        extra["suspension"] = suspension_run(lbeh, stream, peak, peak_kind, args)
-        extra["showcase"] = showcase_run(lbeh, stream, args)
-        extra["coated_droplet"] = coated_run(lbeh, stream, args)
-        extra["batch"] = batch_run(lbeh, stream, args)
-        extra["adjoint"] = adjoint_run(lbeh, stream, args)
+        runs = {"suspension": lambda: suspension_run(lbeh, stream, peak, peak_kind, args, n=args.suspension_size),
+                "showcase": lambda: showcase_run(lbeh, stream, args),
+                "coated_droplet": lambda: coated_run(lbeh, stream, args),
+                "batch": lambda: batch_run(lbeh, stream, args),
+                "adjoint": lambda: adjoint_run(lbeh, stream, args)}
+        want = set(args.extras.split(","))
+        for name in EXTRAS:
+            if name in want:
+                extra[name] = runs[name]()
     cpu = None if args.no_cpu_baseline else cpu_baseline(n)
     clocks = sampler.summary() if sampler else {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
     total_ms = sum(prof["ms"].values())
@@ -538,15 +542,20 @@ def _timed(step, stream, steps):
     return e0.elapsed_time(e1), rc
 
 
+EXTRAS = ("suspension", "showcase", "coated_droplet", "batch", "adjoint")
+
+
 def suspension_run(lbeh, stream, peak, peak_kind, args, n=256, steps=100):
     """256^3 electrophoresis suspension: one fluid, 1e-3 salt, 200 moving
-    charged spheres of radius 6, E_x = 1e-3; FP32 and BF16 storage."""
+    charged spheres of radius 6, E_x = 1e-3; FP32 and BF16 storage.  Other
+    box edges keep the number density of the spheres."""
     import numpy as np
     import synth
-    out = {"workload": "suspension %d^3, 200 moving colloids r=6, salt 1e-3, E_x=1e-3" % n, "steps": steps}
+    ncoll = max(1, int(round(200 * (n / 256.0) ** 3)))
+    out = {"workload": "suspension %d^3, %d moving colloids r=6, salt 1e-3, E_x=1e-3" % (n, ncoll), "steps": steps}
     vx = {}
     for prec in ("fp32", "bf16"):
-        w = synth.suspension(n=n, ncoll=200, r=6.0, prec=prec)
+        w = synth.suspension(n=n, ncoll=ncoll, r=6.0, prec=prec)
         s = lbeh.System(w.params, stream.cuda_stream)
         s.set_fields(rho=list(w.rho), n=list(w.n), colloid_x=w.colloid_x, colloid_v=w.colloid_v,
                      colloid_q=w.colloid_q, colloid_r=w.colloid_r)
@@ -692,6 +701,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the suspension, showcase, coated-droplet, batch and adjoint measurements")
+    ap.add_argument("--extras", default=",".join(EXTRAS),
+                    help="comma-separated extra measurements to run (default: all of %s)" % ", ".join(EXTRAS))
+    ap.add_argument("--suspension-size", type=int, default=256,
+                    help="edge of the suspension box (the sphere count keeps the density of 200 in 256^3)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
