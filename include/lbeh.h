@@ -145,7 +145,10 @@ typedef struct lbeh_obs {
 typedef struct lbeh_handle lbeh_handle;
 
 /* Allocate the device state of one lattice system (model of Sec. II).
- * Copies *p.  Errors: INVALID_ARG (bad sizes or flags), OOM, CUDA. */
+ * Copies *p.  Besides device memory the handle owns two non-blocking streams
+ * (whole-step graph replay; host-to-device copies of lbeh_set_fields), both
+ * ordered against p->stream with events.  Errors: INVALID_ARG (bad sizes or
+ * flags), OOM, CUDA. */
 int lbeh_create(const lbeh_params *p, lbeh_handle **out);
 
 /* Load the state: colloids first (projection of Sec. II.E: solid nodes,
