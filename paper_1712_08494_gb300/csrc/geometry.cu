@@ -62,8 +62,8 @@ __device__ __forceinline__ int wrap_rel(int dx, int n) {
 
 template <typename T>
 __global__ void k_project(Dims d, int h, const double *__restrict__ cx, const double *__restrict__ cr,
-                          uint8_t *__restrict__ solid, int *__restrict__ owner, T *__restrict__ psi_s) {
-  const int j = blockIdx.x;
+                          uint8_t *__restrict__ solid, int *__restrict__ owner, T *__restrict__ psi_s, int slabs) {
+  const int j = blockIdx.x / slabs, sl = blockIdx.x - j * slabs;
   const double X[3] = {cx[3 * j], cx[3 * j + 1], cx[3 * j + 2]};
   const double r = cr[j];
   const double r2 = __dmul_rn(r, r);
@@ -96,7 +96,7 @@ __global__ void k_project(Dims d, int h, const double *__restrict__ cx, const do
   const double reach = 1.7320508075688772 * (0.5 - 0.5 / double(hp)) + 1e-3;
   const double r_in = r - reach, r_out = r + reach;
   const bool shortcut = 2.0 * (r_out + 1.0) < double(min(d.nx, min(d.ny, d.nz)));
-  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+  for (long long t = (long long)sl * blockDim.x + threadIdx.x; t < tot; t += (long long)slabs * blockDim.x) {
     int x, y, z;
     box_site(d, b, t, x, y, z);
     const long long i = site(d, x, y, z);
@@ -147,13 +147,14 @@ __global__ void k_project(Dims d, int h, const double *__restrict__ cx, const do
 template <typename T>
 __global__ void k_surface(Dims d, const double *__restrict__ cx, const double *__restrict__ cr,
                           const uint8_t *__restrict__ solid, const int *__restrict__ owner,
-                          uint8_t *__restrict__ surface, int *__restrict__ count, T *__restrict__ psi_s) {
-  const int j = blockIdx.x;
+                          uint8_t *__restrict__ surface, int *__restrict__ count, T *__restrict__ psi_s,
+                          int slabs) {
+  const int j = blockIdx.x / slabs, sl = blockIdx.x - j * slabs;
   const double X[3] = {cx[3 * j], cx[3 * j + 1], cx[3 * j + 2]};
   const Box b = bbox(d, X, cr[j], 1.0);
   const long long tot = (long long)b.cnt[0] * b.cnt[1] * b.cnt[2];
   int mine = 0;
-  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+  for (long long t = (long long)sl * blockDim.x + threadIdx.x; t < tot; t += (long long)slabs * blockDim.x) {
     int x, y, z;
     box_site(d, b, t, x, y, z);
     const long long i = site(d, x, y, z);
@@ -174,13 +175,14 @@ __global__ void k_surface(Dims d, const double *__restrict__ cx, const double *_
 template <typename T>
 __global__ void k_charge(Dims d, const double *__restrict__ cx, const double *__restrict__ cr,
                          const double *__restrict__ cq, const uint8_t *__restrict__ surface,
-                         const int *__restrict__ owner, const int *__restrict__ count, T *__restrict__ qc) {
-  const int j = blockIdx.x;
+                         const int *__restrict__ owner, const int *__restrict__ count, T *__restrict__ qc,
+                         int slabs) {
+  const int j = blockIdx.x / slabs, sl = blockIdx.x - j * slabs;
   const double X[3] = {cx[3 * j], cx[3 * j + 1], cx[3 * j + 2]};
   const Box b = bbox(d, X, cr[j], 1.0);
   const long long tot = (long long)b.cnt[0] * b.cnt[1] * b.cnt[2];
   const double val = count[j] > 0 ? __ddiv_rn(cq[j], double(count[j])) : 0.0;
-  for (long long t = threadIdx.x; t < tot; t += blockDim.x) {
+  for (long long t = (long long)sl * blockDim.x + threadIdx.x; t < tot; t += (long long)slabs * blockDim.x) {
     int x, y, z;
     box_site(d, b, t, x, y, z);
     const long long i = site(d, x, y, z);
@@ -205,9 +207,12 @@ template <typename T> static void build(Ctx &c) {
   cudaMemsetAsync(c.qc, 0, N * sizeof(T), c.s);
   if (c.ncoll > 0) {
     cudaMemsetAsync(c.ccount, 0, c.ncoll * sizeof(int), c.s);
-    count_launch(), k_project<T><<<c.ncoll, 256, 0, c.s>>>(c.d, c.h, c.cx, c.cr, c.solid, c.owner, (T *)c.psi_s);
-    count_launch(), k_surface<T><<<c.ncoll, 256, 0, c.s>>>(c.d, c.cx, c.cr, c.solid, c.owner, c.surface, c.ccount, (T *)c.psi_s);
-    count_launch(), k_charge<T><<<c.ncoll, 256, 0, c.s>>>(c.d, c.cx, c.cr, c.cq, c.surface, c.owner, c.ccount, (T *)c.qc);
+    const int sl = colloid_slabs(c.ncoll);
+    count_launch(), k_project<T><<<c.ncoll * sl, 256, 0, c.s>>>(c.d, c.h, c.cx, c.cr, c.solid, c.owner, (T *)c.psi_s, sl);
+    count_launch(), k_surface<T><<<c.ncoll * sl, 256, 0, c.s>>>(c.d, c.cx, c.cr, c.solid, c.owner, c.surface, c.ccount,
+                                                                 (T *)c.psi_s, sl);
+    count_launch(), k_charge<T><<<c.ncoll * sl, 256, 0, c.s>>>(c.d, c.cx, c.cr, c.cq, c.surface, c.owner, c.ccount,
+                                                                (T *)c.qc, sl);
   }
   count_launch(), k_psi_f<T><<<grid_for(N, 256), 256, 0, c.s>>>(N, c.solid, (const T *)c.psi_s, (T *)c.psi_f);
   c.geom_empty = c.ncoll == 0;

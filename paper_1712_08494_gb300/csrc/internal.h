@@ -95,6 +95,16 @@ PrecOps ops_f32();
 PrecOps ops_bf16();
 PrecOps ops_f16();
 
+// The projection kernels spread each colloid's bounding box over several
+// blocks (slabs of its cells), about 1024 blocks in all and at most
+// kColloidSlabsMax per colloid; what they accumulate (solid fractions of
+// dyadic values, owner maxima, surface counts) is exact in any order.
+constexpr int kColloidSlabsMax = 16;
+inline int colloid_slabs(int ncoll) {
+  if (ncoll < 1) return 1;
+  const int s = (1024 + ncoll - 1) / ncoll;
+  return s > kColloidSlabsMax ? kColloidSlabsMax : (s < 1 ? 1 : s);
+}
 constexpr int kObsLen = 16;  // see step_kernels.cuh obs layout
 constexpr int kRedBlocks = 512;
 
